@@ -1,0 +1,360 @@
+"""Benchmark of the reconstruction hot path on GB300.
+
+A step is one iteration of greedy coordinate descent (Algorithm 2) through
+the C ABI: FindBest (Algorithm 3) over NNDescent (Algorithm 4) with exact
+FP32 pair gains, the matching-batch coordinate updates, the field sweep and the
+objective.  Default workload: Ising, N=2000 nodes, M=1000 Gibbs-sampled spins
+on a planted random 4-regular graph (couplings +-0.3), k=16, kappa=2.
+
+Printed: one JSON line with pair-sample evaluations per second (value), the
+end-to-end figure through host buffers (e2e), the roofline of the dominant
+kernel (the pair scorer), the CPU oracle baseline, clocks, and the time to
+0.99 best-pair recall.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BYTES_PER_PAIR_SAMPLE = 4.125  # the streamed row of a pair: 4 B of tanh(phi) + 1 bit of x
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ising_n2000_m1000")
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--kappa", type=float, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+
+def _workload(name, rank, device):
+    from paper_2401_01404_gb300 import inputs
+
+    wl = inputs.config(name, device=device)
+    if rank:
+        # independent replica per rank: a new sample draw of the same planted model
+        wl = inputs.ising_workload(name, wl.N, wl.M, "regular" if "n2000" in name else "er",
+                                   4 if "n2000" in name else 5, "pm" if "n2000" in name else "normal",
+                                   0.3, 0.0, 1000, 2000 + 7919 * rank, wl.k, wl.kappa, device)
+    return wl
+
+
+def _cpu_baseline(wl, lam, seconds):
+    """The FP64 oracle (OpenMP on every host core) scoring a bounded sample of
+    uniformly random pairs of the workload at its W = 0 start."""
+    from oracle import oracle
+    from paper_2401_01404_gb300 import inputs
+
+    h = oracle.ising_fields_at_zero(wl.X)
+    phi = np.repeat(h[:, None], wl.M, 1)
+    P = 256
+    t_used = 0.0
+    while True:
+        pairs = inputs.random_pairs(wl.N, P, 77)
+        t0 = time.perf_counter()
+        oracle.ising_score_rows(wl.X, phi, pairs, lam, 5.0)
+        t_used = time.perf_counter() - t0
+        if t_used >= seconds / 4 or P >= 1 << 22:
+            break
+        P *= 4
+    return {"value": P * wl.M / t_used, "unit": "pair-sample evals/s", "cores": oracle.nthreads(),
+            "kind": "oracle",
+            "sample": f"{P} uniformly random pairs of {wl.name} at W=0 (exact gain by FP64 bisection), "
+                      f"{t_used:.1f} s"}
+
+
+def _recall(found, exact, exact_gain, rel_floor=1e-6):
+    """Fraction of the exact best pairs with gain above rel_floor x the largest
+    that the search found (pairs tied at zero gain are left out)."""
+    keep = exact_gain > rel_floor * exact_gain.max()
+    ex = {tuple(p) for p in exact[keep].tolist()}
+    if not ex:
+        return 1.0
+    return len(ex & {tuple(p) for p in found.tolist()}) / len(ex)
+
+
+def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
+    """Time of one FindBest call against its recall@m, for NNDescent iteration
+    caps 1, 2, ...; the first cap reaching 0.99 gives the time to recall."""
+    import torch
+
+    m = int(math.floor(kappa * wl.N + 0.5))
+    ref = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam)
+    top, dtop = ref.exhaustive_best(m)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    ref.exhaustive_best(m)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    t_exh = t0.elapsed_time(t1) / 1e3
+    ref.close()
+    curve = []
+    t_hit = None
+    for cap in range(1, 13):
+        ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5)
+        ctx.best_pairs(k, kappa)  # warm
+        ctx2 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5)
+        t0.record(stream)
+        p, d = ctx2.best_pairs(k, kappa)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        dt = t0.elapsed_time(t1) / 1e3
+        rec = _recall(p, top, -dtop.astype(np.float64))
+        curve.append((cap, round(dt, 6), round(rec, 5)))
+        ctx.close()
+        ctx2.close()
+        if rec >= 0.99 and t_hit is None:
+            t_hit = dt
+            break
+    return {"plain_fp32_s": t_hit, "exhaustive_fp32_s": t_exh, "curve": curve, "m": m}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    import __graft_entry__
+
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2401_01404_gb300 import inputs, recon as R
+
+    wl = _workload(a.workload, rank, "cuda")
+    k = a.k or wl.k
+    kappa = a.kappa or wl.kappa
+    lam = inputs.default_lambda(wl.N, wl.M)
+    stream = torch.cuda.current_stream()
+    X_host = torch.from_numpy(wl.samples_major()).pin_memory()
+    X_dev = X_host.cuda()
+    torch.cuda.synchronize()
+
+    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, timing=1)
+    for _ in range(a.warmup):
+        ctx.gcd_step(k, kappa)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
+    s0 = ctx.stats()
+    clocks = Clocks(torch.cuda.current_device())
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.gcd_step(k, kappa)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    s1 = ctx.stats()
+    t_local = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+    units_local = (s1["pair_evals"] - s0["pair_evals"]) * wl.M
+    score_ms = s1["score_ms"] - s0["score_ms"]
+    score_launches = s1["score_launches"] - s0["score_launches"]
+    score_pairs = s1["score_pairs"] - s0["score_pairs"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    obj = ctx.objective()
+    ctx.close()
+
+    t_max, units = t_local, units_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        uu = torch.tensor([units_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+        t_max, units = tt.item(), uu.item()
+
+    # end to end: init from pinned host samples, one step, model back to the host
+    e2e_steps = max(1, min(a.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_units = 0
+    d2h = 0
+    for _ in range(e2e_steps):
+        c2 = R.Recon(X_host.numpy(), R.RECON_ISING, stream=stream, lam=lam)
+        c2.gcd_step(k, kappa)
+        ij, w, f = c2.get_model()
+        e2e_units += c2.stats()["pair_evals"] * wl.M
+        d2h = ij.nbytes + w.nbytes + f.nbytes + 8
+        c2.close()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    avg_launch_s = score_ms / 1e3 / max(score_launches, 1)
+    bytes_per_launch = BYTES_PER_PAIR_SAMPLE * wl.M * score_pairs / max(score_launches, 1)
+    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    line = {
+        "metric": "pair-sample evals/s",
+        "value": units / t_max,
+        "unit": "pair-sample evals/s",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": t_max / a.steps * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "model": "ising", "N": wl.N, "M": wl.M, "k": k, "kappa": kappa,
+                   "lambda": round(lam, 4), "search": "NNDescent FindBest, exact FP32 gains, random init",
+                   "step": "one GCD iteration (best pairs, coordinate updates, field sweep, objective)",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_units / t_e2e, "unit": "pair-sample evals/s",
+                "h2d_bytes_per_step": int(wl.N * wl.M), "d2h_bytes_per_step": int(d2h),
+                "what": "recon_init from pinned host samples + one GCD step + model to host, per step"},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": "k_score (exact pair gain)", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "bytes_per_pair_sample": BYTES_PER_PAIR_SAMPLE,
+                     "avg_launch_ms": avg_launch_s * 1e3, "launches": int(score_launches),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+        "clocks": ck,
+        "objective_after": obj,
+    }
+    if not a.no_cpu:
+        line["cpu_baseline"] = _cpu_baseline(wl, lam, a.cpu_seconds)
+    if not a.no_recall:
+        line["time_to_recall"] = _recall_curve(R, X_dev, lam, wl, k, kappa, stream)
+        line["time_to_recall"]["chosen_s"] = None
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (the CPU oracle)
+
+def run_reference(a):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2401_01404_gb300 import inputs
+
+    oracle.build()
+    wl = inputs.config(a.workload, device="cpu")
+    lam = inputs.default_lambda(wl.N, wl.M)
+    h = oracle.ising_fields_at_zero(wl.X)
+    phi = np.repeat(h[:, None], wl.M, 1)
+    P = 2048
+    for s in range(a.warmup):
+        oracle.ising_score_rows(wl.X, phi, inputs.random_pairs(wl.N, P, 100 + s), lam, 5.0)
+    t = 0.0
+    for s in range(a.steps):
+        pairs = inputs.random_pairs(wl.N, P, 1000 + s)
+        t0 = time.perf_counter()
+        oracle.ising_score_rows(wl.X, phi, pairs, lam, 5.0)
+        t += time.perf_counter() - t0
+    v = P * a.steps * wl.M / t
+    line = {
+        "impl": "reference",
+        "metric": "pair-sample evals/s", "value": v, "unit": "pair-sample evals/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "model": "ising", "N": wl.N, "M": wl.M},
+        "cpu_baseline": {"value": v, "unit": "pair-sample evals/s", "cores": oracle.nthreads(), "kind": "oracle",
+                         "sample": f"{P} uniformly random pairs per step at W=0, exact gain by FP64 bisection"},
+        "e2e": {"value": v, "unit": "pair-sample evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

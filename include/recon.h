@@ -1,0 +1,226 @@
+/*
+ * recon.h -- C ABI of librecon, the GB300 (sm_103a) hot path of subquadratic
+ * network reconstruction (T. P. Peixoto, "Scalable network reconstruction in
+ * subquadratic time", arXiv:2401.01404).
+ *
+ * The library reconstructs a sparse symmetric coupling matrix W from samples
+ * X by maximising a pseudo-likelihood with a Laplace (L1) prior (App. A),
+ * using greedy coordinate descent (Algorithm 2): each iteration finds the
+ * m = round(kappa*N) pairs (i,j) whose single-coupling update gains the most
+ * (FindBest, Algorithm 3, over an NNDescent k-nearest-neighbour search,
+ * Algorithm 4) and updates only those.
+ *
+ * Conventions shared by every call:
+ *  - Pairs are 0-based int32 node ids, stored as consecutive (i, j) entries.
+ *    Outputs are canonical (i < j).  Inputs may be in either order.
+ *  - d(i,j) is returned as -gain, where gain = max_w pi(W_ij <- w) - pi(W)
+ *    >= 0 is the objective increase of the best update of that coupling.  The
+ *    paper's d(i,j) = -max_w pi(W) (Algorithm 2) differs from it by the
+ *    constant pi(W), so both rank pairs identically; the constant (about
+ *    N*M*log 2 in magnitude) would leave no float resolution for the ranking.
+ *  - All work is ordered on the CUDA stream given to recon_init.  A call that
+ *    returns host outputs has synchronised that stream; a call with device
+ *    outputs only has enqueued its work and returns without waiting, except
+ *    where stated.  Calls on one context must not overlap in host threads.
+ *  - A pointer flagged *_is_device != 0 is a device pointer on the context's
+ *    device; otherwise it is an ordinary host pointer.
+ *  - Every call returns a recon_status; nothing is thrown across the ABI.  On
+ *    failure, recon_last_error() describes the cause.  RECON_ECUDA and
+ *    RECON_ETIMEOUT leave the context unusable (RECON_ESTATE afterwards)
+ *    until it is destroyed.  There is no CPU fallback: without a usable GPU,
+ *    recon_init fails.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct recon_ctx recon_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    RECON_OK = 0,
+    RECON_EINVAL = 1,       /* invalid argument; the message names it */
+    RECON_ENOMEM = 2,       /* device or host allocation failed */
+    RECON_ECUDA = 3,        /* a CUDA call failed */
+    RECON_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    RECON_ESTATE = 5,       /* the context was left unusable by an earlier error */
+    RECON_EUNSUPPORTED = 6  /* the option combination is not supported */
+} recon_status;
+
+typedef enum { RECON_ISING = 0, RECON_GAUSSIAN = 1 } recon_model;
+
+typedef enum {
+    RECON_X_INT8 = 0, /* Ising spins, every value -1 or +1 */
+    RECON_X_FP32 = 1  /* Gaussian samples, finite floats */
+} recon_xtype;
+
+typedef enum {
+    RECON_KNN_NNDESCENT = 0,  /* FindKNN by NNDescent (Algorithm 4) at every level */
+    RECON_KNN_EXHAUSTIVE = 1, /* FindKNN by scoring every pair of the level's node set */
+    RECON_KNN_AUTO = 2        /* exhaustive where it costs fewer pair evaluations */
+} recon_knn_mode;
+
+typedef enum {
+    RECON_SEED_RANDOM = 0, /* random k-out initial lists (Algorithm 4) */
+    RECON_SEED_SCREEN = 1, /* lists seeded from the dense tensor-core gradient screen */
+    RECON_SEED_LEARNED = 2 /* lists seeded from the learned sketch embedding */
+} recon_seed_mode;
+
+typedef struct {
+    double lambda;        /* Laplace prior penalty (App. A), >= 0 */
+    uint64_t seed;        /* seed of every random choice of the search */
+    double eps_knn;       /* NNDescent stops when Delta/(k|S|) < eps_knn (Algorithm 4) */
+    int32_t max_knn_iters;/* NNDescent iteration cap; 0 means 2*ceil(log_{2k}|S|)+2 */
+    float w_clamp;        /* couplings are kept within |W_ij| <= w_clamp (0: model default) */
+    float h_clamp;        /* Ising fields are kept within |h_i| <= h_clamp */
+    int32_t knn_mode;     /* recon_knn_mode */
+    int32_t seed_mode;    /* recon_seed_mode, for the first FindBest level */
+    int32_t screen_c;     /* per-node candidates kept by the screen / learned seeding */
+    int32_t timing;       /* nonzero: time every pair-scoring launch with CUDA events
+                             on the context's stream (see recon_stats.score_ms) */
+    int32_t reserved[7];  /* zero */
+} recon_options;
+
+typedef struct {
+    int64_t pair_evals;       /* pairs scored since init (each counts once per score) */
+    int64_t newton_passes;    /* sample passes beyond the first, summed over pairs */
+    int64_t knn_iters;        /* NNDescent iterations run by the last recon_best_pairs */
+    int32_t levels;           /* FindBest KNN levels of the last recon_best_pairs */
+    int32_t level_k[16];      /* k used at each level */
+    int64_t level_size[17];   /* |S_t| at each level (the last one is exhaustive) */
+    int64_t nnz;              /* stored couplings (including ones set back to zero) */
+    int64_t samples;          /* M */
+    int64_t kernel_launches;  /* kernels this context has launched */
+    int64_t score_launches;   /* pair-scoring launches timed (options.timing) */
+    int64_t score_pairs;      /* pairs those launches scored */
+    double score_ms;          /* their summed device time, from CUDA events */
+} recon_stats;
+
+/* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,
+ * eps_knn = 1e-3, max_knn_iters = 0, w_clamp = 0 (the model's default: 5 for
+ * the Ising model, whose float solver supports |W_ij| <= 8; no clamp for the
+ * Gaussian model), h_clamp = 10, knn_mode = RECON_KNN_NNDESCENT,
+ * seed_mode = RECON_SEED_RANDOM, screen_c = 0, timing = 0. */
+void recon_default_options(recon_options *opt);
+
+/* recon_init -- Sec. II's reconstruction problem for data X and the model's
+ * pseudo-likelihood (App. A), starting from the empty network W = 0 (Sec. II).
+ *   X        : M x N samples, sample-major: X[m*N + i] is node i in sample m.
+ *              int8 spins (-1/+1) for RECON_ISING, float for RECON_GAUSSIAN.
+ *              Read during the call only; the caller keeps ownership and may
+ *              free it when the call returns.
+ *   x_is_device: X is a device pointer (else host).
+ *   opt      : may be NULL for the defaults; copied.
+ *   stream   : a cudaStream_t (NULL = the legacy default stream).
+ * The library copies X into its own node-major device layout, fits the
+ * per-node parameters at W = 0 (Ising fields h_i = atanh(mean x_i) clamped to
+ * h_clamp; Gaussian theta_i^2 = mean x_i^2) and the per-sample fields.
+ * Errors: RECON_EINVAL for N < 2, M < 1, lambda < 0 or not finite, a spin
+ * not in {-1,+1}, a non-finite sample, an unknown model or type;
+ * RECON_ENOMEM; RECON_ECUDA (also when no CUDA device is usable).  On error
+ * *out is NULL. Synchronous. */
+recon_status recon_init(recon_ctx **out, const void *X, int64_t M, int64_t N, int32_t x_type,
+                        int32_t x_is_device, int32_t model, const recon_options *opt, void *stream);
+
+/* recon_objective -- log pi(W, theta) up to its constant: the log
+ * pseudo-likelihood summed over samples and nodes plus the Laplace log-prior
+ * -lambda sum_{i<j} |W_ij| (App. A).  Per-term float, double accumulation.
+ * Synchronous. */
+recon_status recon_objective(recon_ctx *ctx, double *out);
+
+/* recon_score -- d(i,j) = -gain for P pairs at the current (W, theta)
+ * (Algorithm 2's distance; each gain is the exact optimum of the
+ * single-coupling problem under the L1 prior, solved to float precision).
+ *   pairs : P x 2 int32; i != j, both in [0, N).
+ *   d_out : P floats.  w_out: P floats (the maximising W_ij), may be NULL.
+ *   io_is_device: pairs, d_out and w_out are all device pointers (else all host).
+ * Errors: RECON_EINVAL for a bad id or P < 0.  P = 0 is a no-op. */
+recon_status recon_score(recon_ctx *ctx, const int32_t *pairs, int64_t P, float *d_out, float *w_out,
+                         int32_t io_is_device);
+
+/* recon_best_pairs -- FindBest(m, {0..N-1}, d) of Algorithm 3 with
+ * m = round(kappa*N) (half up), over FindKNN by NNDescent (Algorithm 4) or
+ * exhaustive scoring (opt.knn_mode).  At each level k_t = max(k,
+ * ceil(4m/|S_t|)) (at most |S_t|-1); the recursion ends with an exhaustive
+ * search once |S_t|^2 <= 4m.
+ *   pairs : cap x 2 int32, written with min(m, found) canonical pairs in
+ *           ascending d (ties by (i, j)).  d: cap floats (may be NULL).
+ *   *m_out: the number written; when cap < m it is set to m and nothing is
+ *           written (RECON_EINVAL).
+ * Synchronous. */
+recon_status recon_best_pairs(recon_ctx *ctx, int32_t k, double kappa, int32_t *pairs, float *d,
+                              int64_t cap, int64_t *m_out, int32_t out_is_device);
+
+/* recon_exhaustive_best -- the m best pairs over all N(N-1)/2 pairs, exact
+ * (Algorithm 3's exhaustive base case applied to the whole node set); the
+ * ground truth that recall is measured against.  Arguments as in
+ * recon_best_pairs, with m given directly. Synchronous. */
+recon_status recon_exhaustive_best(recon_ctx *ctx, int64_t m, int32_t *pairs, float *d, int64_t cap,
+                                   int64_t *m_out, int32_t out_is_device);
+
+/* recon_cd_sweep -- the update loop of Algorithm 2: each pair's coupling is
+ * set to its maximiser in turn, in the given order, with the per-sample fields
+ * of both endpoints refreshed (App. A's tracked sums).  Pairs that share no
+ * node are updated concurrently (App. B); the result equals the sequential
+ * loop in the given order.  Duplicate pairs are allowed and are applied twice.
+ *   pairs_is_device: pairs is a device pointer (else host).
+ *   delta_out: sum |W_ij' - W_ij| (may be NULL).  Synchronous. */
+recon_status recon_cd_sweep(recon_ctx *ctx, const int32_t *pairs, int64_t P, int32_t pairs_is_device,
+                            double *delta_out);
+
+/* recon_field_sweep -- optimises every per-node parameter theta_i (Ising
+ * field h_i; Gaussian theta_i^2 = 1/W_ii) at fixed couplings, the update that
+ * App. A performs alongside W.  delta_out: sum |theta_i' - theta_i| (may be
+ * NULL). Synchronous. */
+recon_status recon_field_sweep(recon_ctx *ctx, double *delta_out);
+
+/* recon_gcd_step -- one iteration of Algorithm 2: recon_best_pairs(k, kappa),
+ * recon_cd_sweep over them in ascending d, then recon_field_sweep.
+ * delta_out: Delta of the iteration (couplings + per-node parameters);
+ * objective_out: the objective afterwards; m_out: pairs updated.  Any of the
+ * three may be NULL. Synchronous. */
+recon_status recon_gcd_step(recon_ctx *ctx, int32_t k, double kappa, double *delta_out,
+                            double *objective_out, int64_t *m_out);
+
+/* recon_get_model -- the current couplings and per-node parameters.
+ *   ij: cap x 2 int32, w: cap floats; receive the stored couplings (i < j),
+ *   including ones that an update set back to zero; *nnz gets their count
+ *   (when cap < count nothing is written and RECON_EINVAL is returned).
+ *   fields: N floats (Ising h_i; Gaussian theta_i^2), may be NULL.
+ * Host pointers. Synchronous. */
+recon_status recon_get_model(recon_ctx *ctx, int32_t *ij, float *w, int64_t cap, int64_t *nnz,
+                             float *fields);
+
+/* recon_set_model -- replaces the state: couplings W (nnz entries, i != j,
+ * each unordered pair at most once) and per-node parameters (N floats, may be
+ * NULL to keep them), then recomputes the per-sample fields from scratch.
+ * Host pointers. Synchronous. */
+recon_status recon_set_model(recon_ctx *ctx, const int32_t *ij, const float *w, int64_t nnz,
+                             const float *fields);
+
+/* recon_get_stats -- counters (see recon_stats). Host pointer. */
+recon_status recon_get_stats(recon_ctx *ctx, recon_stats *out);
+
+/* recon_save / recon_load -- checkpoint of the whole state (options, samples,
+ * couplings, per-node parameters, counters) in a versioned binary file;
+ * recon_load rebuilds the per-sample fields, so a loaded context continues
+ * exactly as the saved one would. */
+recon_status recon_save(recon_ctx *ctx, const char *path);
+recon_status recon_load(recon_ctx **out, const char *path, void *stream);
+
+/* recon_last_error -- message of the last failed call on ctx (or of the last
+ * failed recon_init / recon_load in this thread when ctx is NULL). */
+const char *recon_last_error(const recon_ctx *ctx);
+
+/* recon_destroy -- frees every resource of ctx; NULL is a no-op. */
+void recon_destroy(recon_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H */

@@ -112,7 +112,7 @@ class IsingOracle:
     """State (W, h) of the Ising pseudo-likelihood problem with its tracked
     fields phi (App. A).  W is dense; fine for the sizes the oracle serves."""
 
-    def __init__(self, X: np.ndarray, lam: float, w_clamp: float = 10.0, h_clamp: float = 10.0,
+    def __init__(self, X: np.ndarray, lam: float, w_clamp: float = 5.0, h_clamp: float = 10.0,
                  dense: bool = True):
         self.X = np.ascontiguousarray(X, dtype=np.int8)
         self.N, self.M = self.X.shape

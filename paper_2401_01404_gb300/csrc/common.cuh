@@ -1,0 +1,312 @@
+// common.cuh -- internal declarations of librecon (not part of the ABI).
+//
+// Device layout (node-major, sized for HBM residency):
+//   Ising:    xbits  uint32 [N x Mw]  bit l of word c is sample 32c+l; 1 <=> x = -1
+//             phi    float  [N x Mp]  per-sample local field h_i + sum_j W_ij x_j
+//             t      float  [N x Mp]  tanh(phi); padding samples hold t = 1
+//             h, H   float  [N]       fields; H_i = sum_m (1 - t_i^2)
+//   Gaussian: xg     float  [N x Mp]  samples (padding 0)
+//             e      float  [N x Mp]  residual x + s2 * mu
+//             mu     float  [N x Mp]  neighbour sums sum_j W_ij x_j
+//             s2, Q  float  [N]       theta_i^2 = 1/W_ii; Q_i = sum_m x_i^2
+//   W: open-addressing hash table of the stored couplings, key (i << 32 | j), i < j.
+// Mp = M rounded up to a multiple of 32; Mw = Mp / 32.  Padding samples
+// (m >= M) have x = +1 and t = 1 for the Ising model, which makes every
+// per-sample term of the pair problem vanish exactly; kernels that touch phi
+// mask them instead.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "recon.h"
+
+#define RECON_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+// SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014): counter-based
+// stream for the random choices of the search, and the hash of the tables.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t pair_key(int a, int b) {
+    uint32_t lo = (uint32_t)(a < b ? a : b), hi = (uint32_t)(a < b ? b : a);
+    return ((uint64_t)lo << 32) | hi;
+}
+
+// Order-preserving map float -> uint32 (ascending floats -> ascending ints).
+__host__ __device__ __forceinline__ uint32_t float_key(float f) {
+    uint32_t u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Hardware reciprocal (rcp.approx, about 1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// coupling table
+// ---------------------------------------------------------------------------
+struct WTable {
+    unsigned long long *keys;  // RECON_EMPTY_KEY when free
+    float *vals;
+    uint64_t mask;             // capacity - 1 (capacity a power of two)
+};
+
+__device__ __forceinline__ float wt_lookup(const WTable &T, uint64_t key) {
+    uint64_t s = mix64(key) & T.mask;
+    for (uint64_t probe = 0; probe <= T.mask; ++probe) {
+        unsigned long long k = T.keys[s];
+        if (k == key) return T.vals[s];
+        if (k == RECON_EMPTY_KEY) return 0.f;
+        s = (s + 1) & T.mask;
+    }
+    return 0.f;
+}
+
+// Inserts or overwrites; returns false when the table is full.
+__device__ __forceinline__ bool wt_upsert(const WTable &T, uint64_t key, float v) {
+    uint64_t s = mix64(key) & T.mask;
+    for (uint64_t probe = 0; probe <= T.mask; ++probe) {
+        unsigned long long k = T.keys[s];
+        if (k == key) { T.vals[s] = v; return true; }
+        if (k == RECON_EMPTY_KEY) {
+            unsigned long long prev = atomicCAS(&T.keys[s], RECON_EMPTY_KEY, (unsigned long long)key);
+            if (prev == RECON_EMPTY_KEY || prev == key) { T.vals[s] = v; return true; }
+        }
+        s = (s + 1) & T.mask;
+    }
+    return false;
+}
+
+// Set insertion; returns 1 if the key was new, 0 if present, -1 if full.
+__device__ __forceinline__ int set_insert(unsigned long long *keys, uint64_t mask, uint64_t key) {
+    uint64_t s = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = keys[s];
+        if (k == key) return 0;
+        if (k == RECON_EMPTY_KEY) {
+            unsigned long long prev = atomicCAS(&keys[s], RECON_EMPTY_KEY, (unsigned long long)key);
+            if (prev == RECON_EMPTY_KEY) return 1;
+            if (prev == key) return 0;
+        }
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+__device__ __forceinline__ bool set_contains(const unsigned long long *keys, uint64_t mask, uint64_t key) {
+    uint64_t s = mix64(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = keys[s];
+        if (k == key) return true;
+        if (k == RECON_EMPTY_KEY) return false;
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// device-resident counters
+// ---------------------------------------------------------------------------
+enum {
+    CNT_PAIR_EVALS = 0,
+    CNT_NEWTON = 1,
+    CNT_ERR = 2,       // bit flags, see ERR_*
+    CNT_SCRATCH0 = 3,  // per-call scratch counters
+    CNT_SCRATCH1 = 4,
+    CNT_SCRATCH2 = 5,
+    CNT_SCRATCH3 = 6,
+    CNT_N = 16
+};
+enum { ERR_BAD_SPIN = 1, ERR_TABLE_FULL = 2, ERR_BAD_VALUE = 4, ERR_OVERFLOW = 8, ERR_TIMEOUT = 16 };
+
+// ---------------------------------------------------------------------------
+// model views passed to kernels
+// ---------------------------------------------------------------------------
+struct IsingView {
+    const uint32_t *xbits;
+    float *phi, *t, *h, *H;
+    int N, M, Mp, Mw;
+};
+
+struct GaussView {
+    const float *xg;
+    float *e, *mu, *s2, *Q;
+    int N, M, Mp;
+};
+
+struct ScoreParams {
+    float lambda, w_clamp, h_clamp;
+};
+
+// ---------------------------------------------------------------------------
+// growable device buffer
+// ---------------------------------------------------------------------------
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct SearchBufs;  // defined in search.cuh
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct recon_ctx {
+    int model = 0, device = 0, num_sms = 0;
+    int64_t N = 0, M = 0, Mp = 0, Mw = 0;
+    recon_options opt{};
+    cudaStream_t stream = nullptr;
+
+    // Ising
+    uint32_t *xbits = nullptr;
+    float *phi = nullptr, *t = nullptr, *h = nullptr, *H = nullptr;
+    // Gaussian
+    float *xg = nullptr, *e = nullptr, *mu = nullptr, *s2 = nullptr, *Q = nullptr;
+    // host copy of the samples (sample-major), kept for checkpoints
+    std::vector<uint8_t> x_host;
+
+    WTable W{};
+    uint64_t w_cap = 0;
+
+    unsigned long long *cnt = nullptr;  // device counters [CNT_N]
+    unsigned long long *cnt_host = nullptr;  // pinned mirror
+
+    std::vector<DBuf> bufs;  // scratch by slot
+    SearchBufs *sb = nullptr;
+
+    recon_stats stats{};
+    uint64_t stats_calls = 0;  // best-pairs calls so far (seeds each call's random choices)
+    std::string err;
+    bool broken = false;
+
+    // per-launch CUDA events of the pair-scoring kernel (options.timing)
+    struct TimedLaunch {
+        cudaEvent_t a, b;
+        int64_t pairs;
+    };
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+
+    IsingView iv() const {
+        return IsingView{xbits, phi, t, h, H, (int)N, (int)M, (int)Mp, (int)Mw};
+    }
+    GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
+    ScoreParams sp() const { return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp}; }
+};
+
+// the context whose API call is running on this thread (for launch counting)
+extern thread_local recon_ctx *tl_ctx;
+inline void note_launch() {
+    if (tl_ctx) tl_ctx->stats.kernel_launches++;
+}
+
+// scratch slots
+enum {
+    BUF_PAIRS = 0, BUF_GAIN, BUF_WST, BUF_BATCH, BUF_ORDER, BUF_OFF, BUF_FIRST, BUF_DELTA, BUF_TMP0,
+    BUF_TMP1, BUF_TMP2, BUF_TMP3, BUF_SORT0, BUF_SORT1, BUF_SORT2, BUF_SORT3, BUF_SORT4, BUF_NSLOTS
+};
+
+// returns false on allocation failure (message set)
+bool ensure_buf(recon_ctx *c, int slot, size_t bytes);
+template <class T>
+static inline T *buf(recon_ctx *c, int slot) {
+    return (T *)c->bufs[slot].p;
+}
+
+// ---------------------------------------------------------------------------
+// launchers (each returns cudaGetLastError())
+// ---------------------------------------------------------------------------
+// ising.cu
+cudaError_t launch_ising_pack(const int8_t *X_sm, int64_t M, int64_t N, int Mw, uint32_t *xbits,
+                              unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_ising_init_fields(IsingView v, float h_clamp, cudaStream_t s);
+cudaError_t launch_ising_phi_from_csr(IsingView v, const int64_t *off, const int32_t *nbr,
+                                      const float *w, cudaStream_t s);
+cudaError_t launch_ising_objective(IsingView v, double *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
+                               const int32_t *gid, float *d_out, float *w_out,
+                               unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                const int32_t *order, int64_t begin, int64_t end, double *delta,
+                                unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_ising_field_sweep(IsingView v, ScoreParams p, double *delta, cudaStream_t s);
+int ising_max_words();
+
+// gauss.cu
+cudaError_t launch_gauss_pack(const float *X_sm, int64_t M, int64_t N, int Mp, float *xg,
+                              unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_gauss_init(GaussView v, cudaStream_t s);
+cudaError_t launch_gauss_mu_from_csr(GaussView v, const int64_t *off, const int32_t *nbr,
+                                     const float *w, cudaStream_t s);
+cudaError_t launch_gauss_objective(GaussView v, double *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_gauss_score(GaussView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
+                               const int32_t *gid, float *d_out, float *w_out,
+                               unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_gauss_update(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                const int32_t *order, int64_t begin, int64_t end, double *delta,
+                                unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_gauss_diag_sweep(GaussView v, double *delta, cudaStream_t s);
+
+// util.cu
+cudaError_t launch_penalty(WTable W, double *out, cudaStream_t s);
+cudaError_t launch_sum_doubles(const double *in, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_layer_batches(const int32_t *pairs, int64_t P, int N, int *first, int *batch,
+                                 int *order, int *boff, int *nb, unsigned long long *cnt,
+                                 cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+cudaError_t launch_table_count(WTable W, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_table_dump(WTable W, int32_t *ij, float *w, unsigned long long *cursor,
+                              cudaStream_t s);
+cudaError_t launch_table_rehash(WTable from, WTable to, cudaStream_t s);
+cudaError_t launch_table_insert(WTable T, const int32_t *ij, const float *w, int64_t n, unsigned long long *cnt,
+                                cudaStream_t s);
+cudaError_t launch_check_pairs(const int32_t *pairs, int64_t P, int n, unsigned long long *cnt, cudaStream_t s);
+// exclusive scan of n int64 counts (tmp holds >= scan_tmp_elems(n) int64)
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+// stable LSD radix sort of (key, value) by key bits [bit0, bit1); ping-pong buffers
+int64_t radix_tmp_elems(int64_t n);
+cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
+                           uint32_t *vals_alt, int64_t n, int bit0, int bit1, int64_t *tmp,
+                           bool *result_in_alt, cudaStream_t s);
+
+// host helpers (api.cu)
+recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...);
+recon_status cuda_fail(recon_ctx *c, cudaError_t e, const char *where);

@@ -1,0 +1,251 @@
+// gauss.cu -- multivariate-Gaussian pseudo-likelihood kernels (App. A of
+// arXiv:2401.01404), the covariance-selection case.
+//
+// Node i's conditional is Normal(-s2_i mu_i, s2_i) with s2_i = theta_i^2 =
+// 1/W_ii and mu_i = sum_{j != i} W_ij x_j.  With the residual
+// e_i = x_i + s2_i mu_i, moving W_ij by delta changes the log pseudo-likelihood
+// by exactly
+//     a delta - b delta^2 / 2,   a = -sum_m (e_i x_j + e_j x_i),
+//                                b = s2_i sum_m x_j^2 + s2_j sum_m x_i^2,
+// so under the Laplace prior the best coupling is the soft threshold
+// w* = sign(z) max(|z| - lambda/b, 0) with z = W_ij + a/b, and its gain is
+// a (w* - W_ij) - b (w* - W_ij)^2/2 - lambda |w*| + lambda |W_ij|.  No
+// iteration is needed: one pass of two dot products per pair.
+// The diagonal (theta_i^2, no prior) maximises
+//     sum_m [-(x_i + u mu_i)^2/(2u)] - (M/2) log u,
+// whose stationarity condition C u^2 + M u - A = 0 (A = sum x_i^2,
+// C = sum mu_i^2) gives u = 2A / (M + sqrt(M^2 + 4AC)).
+#include "common.cuh"
+
+namespace {
+
+__global__ void k_gpack(const float *X, int64_t M, int64_t N, int Mp, float *xg, unsigned long long *cnt) {
+    // one thread per (node, sample); reads are coalesced along nodes
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * (int64_t)Mp) return;
+    int64_t m = e / N, i = e - m * N;
+    float v = 0.f;
+    if (m < M) {
+        v = X[m * N + i];
+        if (!isfinite(v)) {
+            atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_BAD_VALUE);
+            v = 0.f;
+        }
+    }
+    xg[i * Mp + m] = v;
+}
+
+// W = 0: theta_i^2 = mean x_i^2, mu = 0, e = x
+__global__ void k_ginit(GaussView v) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    double q = 0.0;
+    for (int m = lane; m < v.Mp; m += 32) {
+        float x = v.xg[i * v.Mp + m];
+        q += (double)x * x;
+        v.mu[i * v.Mp + m] = 0.f;
+        v.e[i * v.Mp + m] = x;
+    }
+    q = warp_sum_d(q);
+    if (lane == 0) {
+        v.Q[i] = (float)q;
+        v.s2[i] = (float)(q / v.M);
+    }
+}
+
+__global__ void k_gmu_from_csr(GaussView v, const int64_t *off, const int32_t *nbr, const float *w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const float s2 = v.s2[i];
+    for (int m = lane; m < v.Mp; m += 32) {
+        float s = 0.f;
+        for (int64_t q = off[i]; q < off[i + 1]; ++q) s += w[q] * v.xg[(int64_t)nbr[q] * v.Mp + m];
+        v.mu[i * v.Mp + m] = s;
+        v.e[i * v.Mp + m] = v.xg[i * v.Mp + m] + s2 * s;
+    }
+}
+
+__global__ void k_gobjective(GaussView v, double *partials) {
+    __shared__ double red[32];
+    const int64_t total = (int64_t)v.N * v.M;
+    const double half_log_2pi = 0.91893853320467274178;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / v.M;
+        int m = (int)(e - i * v.M);
+        float r = v.e[i * v.Mp + m];
+        float s2 = v.s2[i];
+        acc += (double)(-r * r / (2.f * s2)) - 0.5 * log((double)s2) - half_log_2pi;
+    }
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        r = warp_sum_d(r);
+        if (threadIdx.x == 0) partials[blockIdx.x] = r;
+    }
+}
+
+// a = -sum (e_i x_j + e_j x_i), over float4 chunks (Mp is a multiple of 32)
+__device__ __forceinline__ float gauss_a(const GaussView &v, int i, int j, int lane) {
+    const float4 *xi = (const float4 *)(v.xg + (int64_t)i * v.Mp), *xj = (const float4 *)(v.xg + (int64_t)j * v.Mp);
+    const float4 *ei = (const float4 *)(v.e + (int64_t)i * v.Mp), *ej = (const float4 *)(v.e + (int64_t)j * v.Mp);
+    float acc = 0.f;
+    for (int q = lane; q < v.Mp / 4; q += 32) {
+        float4 a = __ldg(ei + q), b = __ldg(xj + q), c = __ldg(ej + q), d = __ldg(xi + q);
+        acc = fmaf(a.x, b.x, acc);
+        acc = fmaf(a.y, b.y, acc);
+        acc = fmaf(a.z, b.z, acc);
+        acc = fmaf(a.w, b.w, acc);
+        acc = fmaf(c.x, d.x, acc);
+        acc = fmaf(c.y, d.y, acc);
+        acc = fmaf(c.z, d.z, acc);
+        acc = fmaf(c.w, d.w, acc);
+    }
+    return -warp_sum(acc);
+}
+
+__device__ __forceinline__ void gauss_solve(float a, float b, float W0, float lambda, float wclamp, float &gain,
+                                            float &w) {
+    float z = W0 + a / b;
+    float mag = fmaxf(fabsf(z) - lambda / b, 0.f);
+    w = copysignf(fminf(mag, wclamp), z);
+    if (mag == 0.f) w = 0.f;
+    float dl = w - W0;
+    float g = a * dl - 0.5f * b * dl * dl - lambda * fabsf(w) + lambda * fabsf(W0);
+    gain = fmaxf(g, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_gscore(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                int64_t P, const int32_t *gid, float *d_out, float *w_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < P; q += nwarps) {
+        int i = pairs[2 * q], j = pairs[2 * q + 1];
+        if (gid) {
+            i = gid[i];
+            j = gid[j];
+        }
+        float a = gauss_a(v, i, j, lane);
+        float b = v.s2[i] * v.Q[j] + v.s2[j] * v.Q[i];
+        float W0 = wt_lookup(W, pair_key(i, j));
+        float g, w;
+        gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
+        if (lane == 0) {
+            d_out[q] = -g;
+            if (w_out) w_out[q] = w;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gupdate(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
+                                                 unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (q >= end) return;
+    const int pidx = order[q];
+    const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
+    const uint64_t key = pair_key(i, j);
+    const float W0 = wt_lookup(W, key);
+    float a = gauss_a(v, i, j, lane);
+    float b = v.s2[i] * v.Q[j] + v.s2[j] * v.Q[i];
+    float g, w;
+    gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
+    const float dl = w - W0;
+    if (dl != 0.f) {
+        const float s2i = v.s2[i], s2j = v.s2[j];
+        for (int m = lane; m < v.M; m += 32) {
+            float xi = v.xg[(int64_t)i * v.Mp + m], xj = v.xg[(int64_t)j * v.Mp + m];
+            float mi = v.mu[(int64_t)i * v.Mp + m] + dl * xj;
+            float mj = v.mu[(int64_t)j * v.Mp + m] + dl * xi;
+            v.mu[(int64_t)i * v.Mp + m] = mi;
+            v.mu[(int64_t)j * v.Mp + m] = mj;
+            v.e[(int64_t)i * v.Mp + m] = fmaf(s2i, mi, xi);
+            v.e[(int64_t)j * v.Mp + m] = fmaf(s2j, mj, xj);
+        }
+        if (lane == 0 && !wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
+    }
+    if (lane == 0) delta[pidx] = fabs((double)dl);
+}
+
+__global__ void k_gdiag(GaussView v, double *delta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    double C = 0.0;
+    for (int m = lane; m < v.M; m += 32) {
+        double mu = v.mu[i * v.Mp + m];
+        C += mu * mu;
+    }
+    C = warp_sum_d(C);
+    const double A = v.Q[i], M = v.M;
+    const double u = 2.0 * A / (M + sqrt(M * M + 4.0 * A * C));
+    const float uf = (float)u;
+    const float old = v.s2[i];
+    if (uf != old) {
+        for (int m = lane; m < v.M; m += 32)
+            v.e[i * v.Mp + m] = fmaf(uf, v.mu[i * v.Mp + m], v.xg[i * v.Mp + m]);
+    }
+    if (lane == 0) {
+        v.s2[i] = uf;
+        delta[i] = fabs((double)uf - (double)old);
+    }
+}
+
+inline unsigned grid_for(int64_t warps, int threads = 256) {
+    int64_t b = (warps * 32 + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_gauss_pack(const float *X_sm, int64_t M, int64_t N, int Mp, float *xg, unsigned long long *cnt,
+                              cudaStream_t s) {
+    int64_t n = N * (int64_t)Mp;
+    k_gpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X_sm, M, N, Mp, xg, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_init(GaussView v, cudaStream_t s) {
+    k_ginit<<<grid_for(v.N), 256, 0, s>>>(v); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_mu_from_csr(GaussView v, const int64_t *off, const int32_t *nbr, const float *w,
+                                     cudaStream_t s) {
+    k_gmu_from_csr<<<grid_for(v.N), 256, 0, s>>>(v, off, nbr, w); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_objective(GaussView v, double *partials, int nblocks, cudaStream_t s) {
+    k_gobjective<<<nblocks, 256, 0, s>>>(v, partials); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_score(GaussView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
+                               const int32_t *gid, float *d_out, float *w_out, unsigned long long *cnt,
+                               cudaStream_t s) {
+    (void)cnt;
+    if (P <= 0) return cudaSuccess;
+    int64_t cap = (int64_t)1 << 20;
+    k_gscore<<<grid_for(P < cap ? P : cap), 256, 0, s>>>(v, W, p, pairs, P, gid, d_out, w_out); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_update(GaussView v, WTable W, ScoreParams p, const int32_t *pairs, const int32_t *order,
+                                int64_t begin, int64_t end, double *delta, unsigned long long *cnt,
+                                cudaStream_t s) {
+    if (end <= begin) return cudaSuccess;
+    k_gupdate<<<grid_for(end - begin), 256, 0, s>>>(v, W, p, pairs, order, begin, end, delta, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_diag_sweep(GaussView v, double *delta, cudaStream_t s) {
+    k_gdiag<<<grid_for(v.N), 256, 0, s>>>(v, delta); note_launch();
+    return cudaGetLastError();
+}

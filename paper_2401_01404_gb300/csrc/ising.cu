@@ -1,0 +1,586 @@
+// ising.cu -- Ising pseudo-likelihood kernels (App. A of arXiv:2401.01404).
+//
+// The pair problem.  Moving W_ij by delta shifts phi_i by delta*x_j and phi_j
+// by delta*x_i in every sample.  With x = +-1 and tau = tanh(delta),
+//     log cosh(phi + delta x) = log cosh(phi) + log cosh(delta) + log(1 + x tanh(phi) tau),
+// so the change of the log pseudo-likelihood is a sum over samples of terms in
+// u = x_j t_i and v = x_i t_j (t = tanh phi):
+//     F(delta)  = sum_m [2 delta x_i x_j - 2 log cosh delta - log(1+tau u) - log(1+tau v)]
+//     F'(delta) = 2 sum x_i x_j - sum [(u+tau)/(1+tau u) + (v+tau)/(1+tau v)]
+//    -F''(delta)= (1 - tau^2) sum [(1-u^2)/(1+tau u)^2 + (1-v^2)/(1+tau v)^2]   (> 0)
+// The gain of the best update under the Laplace prior (App. A) is
+//     max_w F(w - W_ij) - lambda |w| + lambda |W_ij|,
+// a concave 1-D problem: w = 0 when |F'(-W_ij)| <= lambda, otherwise the root
+// of F'(w - W_ij) = lambda sign(w), found by Newton's method safeguarded by a
+// bracket.  F is evaluated as delta*F'(0) plus per-sample remainders that are
+// O(delta^2), never as a difference of two large sums.
+//
+// Thread mapping: one warp per pair; lane l holds samples 32c + l.  Rows of up
+// to 1024 samples live in registers for the whole solve; longer rows are
+// re-read from L1/L2 on every pass.
+#include "common.cuh"
+
+namespace {
+
+constexpr int MAX_NEWTON = 40;
+
+// -------- row sources ------------------------------------------------------
+
+template <int NW>
+struct RegRows {  // both rows in registers (NW words of 32 samples)
+    static constexpr int kNW = NW;
+    float ti[NW], tj[NW];
+    uint32_t pi, pj;  // bit c: x = -1 at sample 32c + lane
+    int Mw;
+    __device__ __forceinline__ void load(const IsingView &v, int i, int j, int lane) {
+        Mw = v.Mw;
+        const float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
+        const uint32_t *Bi = v.xbits + (int64_t)i * v.Mw, *Bj = v.xbits + (int64_t)j * v.Mw;
+        pi = pj = 0u;
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            if (c < Mw) {
+                ti[c] = __ldg(Ti + 32 * c + lane);
+                tj[c] = __ldg(Tj + 32 * c + lane);
+                pi |= ((__ldg(Bi + c) >> lane) & 1u) << c;
+                pj |= ((__ldg(Bj + c) >> lane) & 1u) << c;
+            } else {
+                ti[c] = tj[c] = 1.f;
+            }
+        }
+    }
+    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb) const {
+        a = ti[c];
+        b = tj[c];
+        sa = (pi << (31 - c)) & 0x80000000u;
+        sb = (pj << (31 - c)) & 0x80000000u;
+    }
+};
+
+struct GlobRows {  // rows re-read every pass
+    static constexpr int kNW = 0;
+    const float *Ti, *Tj;
+    const uint32_t *Bi, *Bj;
+    int Mw, lane;
+    __device__ __forceinline__ void load(const IsingView &v, int i, int j, int l) {
+        Mw = v.Mw;
+        lane = l;
+        Ti = v.t + (int64_t)i * v.Mp;
+        Tj = v.t + (int64_t)j * v.Mp;
+        Bi = v.xbits + (int64_t)i * v.Mw;
+        Bj = v.xbits + (int64_t)j * v.Mw;
+    }
+    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb) const {
+        a = __ldg(Ti + 32 * c + lane);
+        b = __ldg(Tj + 32 * c + lane);
+        sa = (__ldg(Bi + c) << (31 - lane)) & 0x80000000u;
+        sb = (__ldg(Bj + c) << (31 - lane)) & 0x80000000u;
+    }
+};
+
+template <class RS, class F>
+__device__ __forceinline__ void for_words(const RS &R, F &&body) {
+    if constexpr (RS::kNW > 0) {
+#pragma unroll
+        for (int c = 0; c < RS::kNW; ++c)
+            if (c < R.Mw) body(c);
+    } else {
+        for (int c = 0; c < R.Mw; ++c) body(c);
+    }
+}
+
+__device__ __forceinline__ float flip(float t, uint32_t s) { return __uint_as_float(__float_as_uint(t) ^ s); }
+
+// log cosh(d) without cancellation at either end
+__device__ __forceinline__ float logcosh_f(float d) {
+    float a = fabsf(d);
+    if (a < 0.5f) {
+        float tt = tanhf(a);
+        return -0.5f * log1pf(-tt * tt);
+    }
+    return a - 0.693147180559945309f + log1pf(expf(-2.f * a));
+}
+
+// pass at delta = 0: sum u, sum v, and the count of disagreeing spins
+template <class RS>
+__device__ __forceinline__ void pass0(const RS &R, float &su, float &sv, int &dis) {
+    float a = 0.f, b = 0.f;
+    int d = 0;
+    for_words(R, [&](int c) {
+        float ti, tj;
+        uint32_t si, sj;
+        R.get(c, ti, tj, si, sj);
+        a += flip(ti, sj);
+        b += flip(tj, si);
+        d += (int)((si ^ sj) >> 31);
+    });
+    su = warp_sum(a);
+    sv = warp_sum(b);
+    dis = warp_sum_i(d);
+}
+
+// d1 = sum [(u+tau)/(1+tau u) + (v+tau)/(1+tau v)], d2 = sum [(1-u^2)/(1+tau u)^2 + ...]
+template <class RS>
+__device__ __forceinline__ void pass_newton(const RS &R, float tau, float &d1, float &d2) {
+    float a1 = 0.f, a2 = 0.f;
+    for_words(R, [&](int c) {
+        float ti, tj;
+        uint32_t si, sj;
+        R.get(c, ti, tj, si, sj);
+        float u = flip(ti, sj), v = flip(tj, si);
+        float ru = rcp_approx(fmaf(tau, u, 1.f));
+        float rv = rcp_approx(fmaf(tau, v, 1.f));
+        a1 = fmaf(u + tau, ru, a1);
+        a1 = fmaf(v + tau, rv, a1);
+        a2 = fmaf(fmaf(-u, u, 1.f), ru * ru, a2);
+        a2 = fmaf(fmaf(-v, v, 1.f), rv * rv, a2);
+    });
+    d1 = warp_sum(a1);
+    d2 = warp_sum(a2);
+}
+
+// q = sum [(delta u - log(1+tau u)) + (delta v - log(1+tau v))]
+template <class RS>
+__device__ __forceinline__ float pass_gain(const RS &R, float delta, float tau) {
+    float q = 0.f;
+    for_words(R, [&](int c) {
+        float ti, tj;
+        uint32_t si, sj;
+        R.get(c, ti, tj, si, sj);
+        float u = flip(ti, sj), v = flip(tj, si);
+        q += fmaf(delta, u, -log1pf(tau * u));
+        q += fmaf(delta, v, -log1pf(tau * v));
+    });
+    return warp_sum(q);
+}
+
+// The whole 1-D problem for one pair (all lanes of the warp participate and
+// end with identical results).
+template <class RS>
+__device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, float W0, float lambda,
+                                           float wclamp, float &gain, float &wstar, int &passes) {
+    float su, sv;
+    int dis;
+    pass0(R, su, sv, dis);
+    const float twoA = 2.f * (float)(Mp - 2 * dis);
+    const float D0 = twoA - su - sv;  // F'(0)
+    passes = 0;
+    float Dz, Dz2;  // F' and -F'' at w = 0
+    if (W0 == 0.f) {
+        Dz = D0;
+        Dz2 = Hsum;
+    } else {
+        float tz = tanhf(-W0), d1, d2;
+        pass_newton(R, tz, d1, d2);
+        ++passes;
+        Dz = twoA - d1;
+        Dz2 = (1.f - tz * tz) * d2;
+    }
+    float w = 0.f;
+    if (fabsf(Dz) > lambda) {
+        const float s = Dz > 0.f ? 1.f : -1.f;
+        // G(u) = s F'(s u - W0) - lambda is decreasing in the magnitude u >= 0
+        float lo = 0.f, hi = wclamp, u = 0.f;
+        float G = s * Dz - lambda, Gp = fmaxf(Dz2, 1e-30f);
+        bool hi_seen = false;
+        for (int it = 0; it < MAX_NEWTON; ++it) {
+            float un = u + G / Gp;
+            if (!(un > lo && un < hi)) un = hi_seen ? 0.5f * (lo + hi) : hi;
+            float step = fabsf(un - u);
+            u = un;
+            float delta = s * u - W0, tau = tanhf(delta), d1, d2;
+            pass_newton(R, tau, d1, d2);
+            ++passes;
+            G = s * (twoA - d1) - lambda;
+            Gp = fmaxf((1.f - tau * tau) * d2, 1e-30f);
+            if (G > 0.f) {
+                lo = u;
+                if (u >= wclamp) break;  // the optimum lies beyond the clamp
+            } else {
+                hi = u;
+                hi_seen = true;
+            }
+            float tol = 2e-5f * fmaxf(u, 0.05f);
+            if (step <= tol || (hi_seen && hi - lo <= tol)) break;
+        }
+        w = s * u;
+    }
+    const float dl = w - W0;
+    float g = 0.f;
+    if (dl != 0.f) {
+        float tau = tanhf(dl);
+        float q = pass_gain(R, dl, tau);
+        ++passes;
+        float F = dl * D0 + q - 2.f * (float)Mp * logcosh_f(dl);
+        g = F - lambda * fabsf(w) + lambda * fabsf(W0);
+    }
+    gain = fmaxf(g, 0.f);
+    wstar = w;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_pack(const int8_t *X, int64_t M, int64_t N, int Mw, uint32_t *xbits,
+                       unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ngroups = (N + 31) / 32;
+    if (w >= ngroups * Mw) return;
+    const int64_t g = w / Mw;
+    const int c = (int)(w % Mw);
+    const int64_t i = g * 32 + lane;
+    if (i >= N) return;
+    uint32_t word = 0;
+    bool bad = false;
+    for (int s = 0; s < 32; ++s) {
+        int64_t m = (int64_t)c * 32 + s;
+        if (m < M) {
+            int8_t x = X[m * N + i];
+            if (x == -1)
+                word |= 1u << s;
+            else if (x != 1)
+                bad = true;
+        }
+    }
+    xbits[i * Mw + c] = word;
+    if (bad) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_BAD_SPIN);
+}
+
+// W = 0 field optimum: sum_m (x - tanh h) = 0  =>  h = atanh(mean x), clamped
+__global__ void k_init_fields(IsingView v, float h_clamp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    int neg = 0;
+    for (int c = lane; c < v.Mw; c += 32) neg += __popc(v.xbits[i * v.Mw + c]);
+    neg = warp_sum_i(neg);
+    double xbar = (double)(v.M - 2 * neg) / (double)v.M;
+    double hh;
+    if (xbar >= 1.0)
+        hh = h_clamp;
+    else if (xbar <= -1.0)
+        hh = -h_clamp;
+    else {
+        hh = 0.5 * log((1.0 + xbar) / (1.0 - xbar));
+        hh = fmin(fmax(hh, -(double)h_clamp), (double)h_clamp);
+    }
+    float h = (float)hh, th = tanhf(h);
+    float hs = 0.f;
+    for (int m = lane; m < v.Mp; m += 32) {
+        bool real = m < v.M;
+        v.phi[i * v.Mp + m] = real ? h : 0.f;
+        v.t[i * v.Mp + m] = real ? th : 1.f;
+        if (real) hs += 1.f - th * th;
+    }
+    hs = warp_sum(hs);
+    if (lane == 0) {
+        v.h[i] = h;
+        v.H[i] = hs;
+    }
+}
+
+// phi_i = h_i + sum_j W_ij x_j from a CSR of the couplings (deterministic order)
+__global__ void k_phi_from_csr(IsingView v, const int64_t *off, const int32_t *nbr, const float *w) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    float hs = 0.f;
+    const float hi = v.h[i];
+    for (int m = lane; m < v.Mp; m += 32) {
+        if (m >= v.M) {
+            v.phi[i * v.Mp + m] = 0.f;
+            v.t[i * v.Mp + m] = 1.f;
+            continue;
+        }
+        float s = hi;
+        for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+            int j = nbr[e];
+            uint32_t bit = (v.xbits[(int64_t)j * v.Mw + (m >> 5)] >> (m & 31)) & 1u;
+            s += bit ? -w[e] : w[e];
+        }
+        float tt = tanhf(s);
+        v.phi[i * v.Mp + m] = s;
+        v.t[i * v.Mp + m] = tt;
+        hs += 1.f - tt * tt;
+    }
+    hs = warp_sum(hs);
+    if (lane == 0) v.H[i] = hs;
+}
+
+// sum over nodes and samples of x phi - log(2 cosh phi): float terms, double sums
+__global__ void k_objective(IsingView v, double *partials) {
+    __shared__ double red[32];
+    const int64_t total = (int64_t)v.N * v.M;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / v.M;
+        int m = (int)(e - i * v.M);
+        float p = v.phi[i * v.Mp + m];
+        uint32_t bit = (v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u;
+        // x phi - log 2cosh phi = (x phi - |phi|) - log(1 + e^{-2|phi|}); the
+        // first term is exactly 0 or -2|phi|
+        float a = fabsf(p);
+        float xp = bit ? -p : p;
+        acc += (double)(xp - a) - (double)log1pf(expf(-2.f * a));
+    }
+    acc = warp_sum_d(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double r = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        r = warp_sum_d(r);
+        if (threadIdx.x == 0) partials[blockIdx.x] = r;
+    }
+}
+
+template <class RS>
+__global__ void __launch_bounds__(256) k_score(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                               int64_t P, const int32_t *gid, float *d_out, float *w_out,
+                                               unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long npass = 0;
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < P; q += nwarps) {
+        int i = pairs[2 * q], j = pairs[2 * q + 1];
+        if (gid) {
+            i = gid[i];
+            j = gid[j];
+        }
+        RS R;
+        R.load(v, i, j, lane);
+        float W0 = wt_lookup(W, pair_key(i, j));
+        float g, w;
+        int passes;
+        solve_pair(R, v.Mp, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
+        if (lane == 0) {
+            d_out[q] = -g;
+            if (w_out) w_out[q] = w;
+            npass += (unsigned long long)passes;
+        }
+    }
+    if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
+}
+
+// One matching batch of Algorithm 2's updates: pairs order[begin..end) share no
+// node, so their row updates are independent.
+template <class RS>
+__global__ void __launch_bounds__(256) k_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                const int32_t *order, int64_t begin, int64_t end,
+                                                double *delta, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (q >= end) return;
+    const int pidx = order[q];
+    const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
+    RS R;
+    R.load(v, i, j, lane);
+    const uint64_t key = pair_key(i, j);
+    const float W0 = wt_lookup(W, key);
+    float g, w;
+    int passes;
+    solve_pair(R, v.Mp, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
+    const float dl = w - W0;
+    if (dl != 0.f) {
+        const uint32_t *Bi = v.xbits + (int64_t)i * v.Mw, *Bj = v.xbits + (int64_t)j * v.Mw;
+        float *Pi = v.phi + (int64_t)i * v.Mp, *Pj = v.phi + (int64_t)j * v.Mp;
+        float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
+        float hi = 0.f, hj = 0.f;
+        for (int c = 0; c < v.Mw; ++c) {
+            int m = 32 * c + lane;
+            if (m >= v.M) break;
+            bool xi_neg = (Bi[c] >> lane) & 1u, xj_neg = (Bj[c] >> lane) & 1u;
+            float pi = Pi[m] + (xj_neg ? -dl : dl);
+            float pj = Pj[m] + (xi_neg ? -dl : dl);
+            float a = tanhf(pi), b = tanhf(pj);
+            Pi[m] = pi;
+            Pj[m] = pj;
+            Ti[m] = a;
+            Tj[m] = b;
+            hi += 1.f - a * a;
+            hj += 1.f - b * b;
+        }
+        hi = warp_sum(hi);
+        hj = warp_sum(hj);
+        if (lane == 0) {
+            v.H[i] = hi;
+            v.H[j] = hj;
+            if (!wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
+        }
+    }
+    if (lane == 0) {
+        delta[pidx] = fabs((double)dl);
+        atomicAdd(&cnt[CNT_NEWTON], (unsigned long long)passes);
+    }
+}
+
+// Field sweep: h_i' = argmax sum_m [x phi - log 2cosh phi] with phi shifted by
+// h_i' - h_i; sum_m (x - tanh(phi + D)) = 0 by safeguarded Newton using
+// tanh(phi + D) = (t + T)/(1 + t T), T = tanh D.
+template <int NW>
+__global__ void __launch_bounds__(256) k_field(IsingView v, ScoreParams p, double *delta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const float *Ti = v.t + i * v.Mp;
+    const uint32_t *Bi = v.xbits + i * v.Mw;
+    float tr[NW], xr[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        int m = 32 * c + lane;
+        bool real = c < v.Mw && m < v.M;
+        tr[c] = real ? Ti[m] : 0.f;
+        xr[c] = real ? (((Bi[c] >> lane) & 1u) ? -1.f : 1.f) : 0.f;  // 0 masks padding
+    }
+    auto eval = [&](float T, float &S, float &Sp) {
+        float a = 0.f, b = 0.f;
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            if (c < v.Mw) {
+                float r = rcp_approx(fmaf(tr[c], T, 1.f));
+                float mask = xr[c] != 0.f ? 1.f : 0.f;
+                a += mask * (xr[c] - (tr[c] + T) * r);
+                b += mask * fmaf(-tr[c], tr[c], 1.f) * r * r;
+            }
+        }
+        S = warp_sum(a);
+        Sp = (1.f - T * T) * warp_sum(b);
+    };
+    const float h0 = v.h[i], hc = p.h_clamp;
+    float S, Sp;
+    eval(0.f, S, Sp);
+    float lo = -hc, hi = hc, hcur = h0;  // bracket on the new value h'
+    bool lo_seen = false, hi_seen = false;
+    if (S > 0.f) { lo = h0; lo_seen = true; } else if (S < 0.f) { hi = h0; hi_seen = true; }
+    if (S != 0.f) {
+        for (int it = 0; it < MAX_NEWTON; ++it) {
+            float hn = hcur + S / fmaxf(Sp, 1e-30f);
+            if (!(hn > lo && hn < hi)) {
+                if (lo_seen && hi_seen) hn = 0.5f * (lo + hi);
+                else hn = lo_seen ? hi : lo;  // try the clamp on the open side
+            }
+            float step = fabsf(hn - hcur);
+            hcur = hn;
+            eval(tanhf(hcur - h0), S, Sp);
+            if (S > 0.f) {
+                lo = hcur;
+                lo_seen = true;
+                if (hcur >= hc) break;
+            } else if (S < 0.f) {
+                hi = hcur;
+                hi_seen = true;
+                if (hcur <= -hc) break;
+            } else
+                break;
+            float tol = 2e-6f * fmaxf(fabsf(hcur), 1.f);
+            if (step <= tol || (lo_seen && hi_seen && hi - lo <= tol)) break;
+        }
+    }
+    const float dh = hcur - h0;
+    if (dh != 0.f) {
+        float *Pi = v.phi + i * v.Mp;
+        float *Tw = v.t + i * v.Mp;
+        float hs = 0.f;
+        for (int m = lane; m < v.M; m += 32) {
+            float ph = Pi[m] + dh, tt = tanhf(ph);
+            Pi[m] = ph;
+            Tw[m] = tt;
+            hs += 1.f - tt * tt;
+        }
+        hs = warp_sum(hs);
+        if (lane == 0) {
+            v.h[i] = hcur;
+            v.H[i] = hs;
+        }
+    }
+    if (lane == 0) delta[i] = fabs((double)dh);
+}
+
+inline unsigned grid_for(int64_t warps, int threads = 256) {
+    int64_t b = (warps * 32 + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int ising_max_words() { return 32; }
+
+cudaError_t launch_ising_pack(const int8_t *X_sm, int64_t M, int64_t N, int Mw, uint32_t *xbits,
+                              unsigned long long *cnt, cudaStream_t s) {
+    int64_t warps = ((N + 31) / 32) * Mw;
+    k_pack<<<grid_for(warps), 256, 0, s>>>(X_sm, M, N, Mw, xbits, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_init_fields(IsingView v, float h_clamp, cudaStream_t s) {
+    k_init_fields<<<grid_for(v.N), 256, 0, s>>>(v, h_clamp); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_phi_from_csr(IsingView v, const int64_t *off, const int32_t *nbr, const float *w,
+                                      cudaStream_t s) {
+    k_phi_from_csr<<<grid_for(v.N), 256, 0, s>>>(v, off, nbr, w); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_objective(IsingView v, double *partials, int nblocks, cudaStream_t s) {
+    k_objective<<<nblocks, 256, 0, s>>>(v, partials); note_launch();
+    return cudaGetLastError();
+}
+
+#define DISPATCH_ROWS(MW, CALL)        \
+    do {                               \
+        if ((MW) <= 4) {               \
+            using RS = RegRows<4>;     \
+            CALL;                      \
+        } else if ((MW) <= 8) {        \
+            using RS = RegRows<8>;     \
+            CALL;                      \
+        } else if ((MW) <= 16) {       \
+            using RS = RegRows<16>;    \
+            CALL;                      \
+        } else if ((MW) <= 32) {       \
+            using RS = RegRows<32>;    \
+            CALL;                      \
+        } else {                       \
+            using RS = GlobRows;       \
+            CALL;                      \
+        }                              \
+    } while (0)
+
+cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
+                               const int32_t *gid, float *d_out, float *w_out, unsigned long long *cnt,
+                               cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    int64_t want = P;
+    int64_t cap = (int64_t)1 << 20;  // warps; grid-stride beyond
+    unsigned grid = grid_for(want < cap ? want : cap);
+    DISPATCH_ROWS(v.Mw, (k_score<RS><<<grid, 256, 0, s>>>(v, W, p, pairs, P, gid, d_out, w_out, cnt))); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, const int32_t *order,
+                                int64_t begin, int64_t end, double *delta, unsigned long long *cnt,
+                                cudaStream_t s) {
+    if (end <= begin) return cudaSuccess;
+    unsigned grid = grid_for(end - begin);
+    DISPATCH_ROWS(v.Mw, (k_update<RS><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, end, delta, cnt))); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_field_sweep(IsingView v, ScoreParams p, double *delta, cudaStream_t s) {
+    unsigned grid = grid_for(v.N);
+    if (v.Mw > 32) return cudaErrorInvalidValue;
+    if (v.Mw <= 4)
+        k_field<4><<<grid, 256, 0, s>>>(v, p, delta);
+    else if (v.Mw <= 8)
+        k_field<8><<<grid, 256, 0, s>>>(v, p, delta);
+    else if (v.Mw <= 16)
+        k_field<16><<<grid, 256, 0, s>>>(v, p, delta);
+    else
+        k_field<32><<<grid, 256, 0, s>>>(v, p, delta);
+    note_launch();
+    return cudaGetLastError();
+}

@@ -1,0 +1,1046 @@
+// search.cu -- FindBest (Algorithm 3) over FindKNN by NNDescent (Algorithm 4)
+// or exhaustive scoring, on the GPU.
+//
+// NNDescent, GPU form.  Every node owns its k-list (kept sorted by d; App. B
+// notes that the per-node list updates need no synchronisation).  One
+// iteration:
+//   1. U = the undirected version of G: each node's k out-neighbours plus at
+//      most k of its in-neighbours, sampled afresh every iteration (the cap on
+//      second neighbours of Sec. III);
+//   2. candidates of x: second neighbours v in U(U(x)) with v > x, deduplicated
+//      in shared memory, minus x's own list; a candidate is generated only if
+//      one of the two U-edges that lead to it is new since the last iteration,
+//      so a pair reached along the same path is scored once (the role of the
+//      score cache of App. B);
+//   3. each canonical candidate pair is scored once (the exact gain) and
+//      offered to both endpoints if it beats their worst entry;
+//   4. each list becomes the best k of (old list u offers), old entries winning
+//      ties (Algorithm 4 replaces only on strict improvement); Delta counts the
+//      entries that are new.
+// The loop stops when Delta/(k|S|) < eps or after the iteration cap.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "search.cuh"
+
+namespace {
+
+constexpr int NND_MAX_K = 32;
+
+__device__ __forceinline__ bool key_less(float da, uint32_t ra, float db, uint32_t rb) {
+    return da < db || (da == db && ra < rb);
+}
+
+// random k-out lists (k distinct ids != x), or every other node when k >= n-1
+__global__ void k_knn_init(int n, int k, uint64_t seed, int32_t *ids) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    int32_t *L = ids + (int64_t)x * k;
+    int q = 0;
+    if (k >= n - 1) {
+        for (int y = 0; y < n && q < k; ++y)
+            if (y != x) L[q++] = y;
+        return;
+    }
+    uint64_t ctr = 0;
+    while (q < k && ctr < 64ull * (uint64_t)k) {
+        uint64_t r = mix64(seed ^ mix64(((uint64_t)x << 32) ^ ctr++));
+        int y = (int)(r % (uint64_t)n);
+        if (y == x) continue;
+        bool dup = false;
+        for (int p = 0; p < q; ++p) dup |= L[p] == y;
+        if (!dup) L[q++] = y;
+    }
+    for (int y = 0; q < k && y < n; ++y) {
+        if (y == x) continue;
+        bool dup = false;
+        for (int p = 0; p < q; ++p) dup |= L[p] == y;
+        if (!dup) L[q++] = y;
+    }
+}
+
+__global__ void k_list_pairs(int n, int k, const int32_t *ids, int32_t *pairs) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    pairs[2 * e] = (int32_t)(e / k);
+    pairs[2 * e + 1] = ids[e];
+}
+
+// sort each initial list by (d, pair hash); every entry is new
+__global__ void k_sort_lists(int n, int k, const int32_t *gid, int32_t *ids, float *dd, uint8_t *isnew) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    int32_t *L = ids + (int64_t)x * k;
+    float *D = dd + (int64_t)x * k;
+    for (int a = 1; a < k; ++a) {
+        int32_t id = L[a];
+        float d = D[a];
+        uint32_t r = (uint32_t)(mix64(pair_key(gid[x], gid[id])) >> 33);
+        int b = a - 1;
+        while (b >= 0) {
+            uint32_t rb = (uint32_t)(mix64(pair_key(gid[x], gid[L[b]])) >> 33);
+            if (!key_less(d, r, D[b], rb)) break;
+            L[b + 1] = L[b];
+            D[b + 1] = D[b];
+            --b;
+        }
+        L[b + 1] = id;
+        D[b + 1] = d;
+    }
+    for (int a = 0; a < k; ++a) isnew[(int64_t)x * k + a] = 1;
+}
+
+__global__ void k_in_count(int64_t nk, const int32_t *ids, int32_t *indeg) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nk) atomicAdd(&indeg[ids[e]], 1);
+}
+
+__global__ void k_i32_to_i64(const int32_t *a, int64_t *b, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) b[e] = a[e];
+}
+
+__global__ void k_in_fill(int64_t nk, const int32_t *ids, const int64_t *inoff, int32_t *cursor, int32_t *in_e) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nk) return;
+    int y = ids[e];
+    int pos = atomicAdd(&cursor[y], 1);
+    in_e[inoff[y] + pos] = (int32_t)e;
+}
+
+// U(x) = out(x) u (at most in_cap in-neighbours, smallest random priority)
+__global__ void k_build_U(int n, int k, int in_cap, int Ucap, uint64_t seed, const int32_t *ids,
+                          const uint8_t *isnew, const int64_t *inoff, const int32_t *indeg, const int32_t *in_e,
+                          int32_t *U, uint8_t *Uf, int32_t *Udeg) {
+    extern __shared__ int32_t sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (x >= n) return;
+    int32_t *sid = sm + wib * 2 * Ucap;
+    int32_t *sfl = sid + Ucap;
+    for (int r = lane; r < k; r += 32) {
+        sid[r] = ids[(int64_t)x * k + r];
+        sfl[r] = isnew[(int64_t)x * k + r];
+    }
+    __syncwarp();
+    int d = k;
+    const int64_t b = inoff[x];
+    const int deg = indeg[x];
+    const int take = deg < in_cap ? deg : in_cap;
+    uint64_t last = 0;
+    for (int s = 0; s < take; ++s) {
+        int e_sel;
+        if (deg <= in_cap) {
+            e_sel = in_e[b + s];
+        } else {
+            uint64_t best = ~0ull;
+            int best_e = -1;
+            for (int q = lane; q < deg; q += 32) {
+                int e = in_e[b + q];
+                uint64_t pr = mix64(seed ^ ((uint64_t)x << 32) ^ (uint64_t)(e / k));
+                if ((s == 0 || pr > last) && (pr < best || (pr == best && e < best_e))) {
+                    best = pr;
+                    best_e = e;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                uint64_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int oe = __shfl_xor_sync(0xffffffffu, best_e, o);
+                if (ob < best || (ob == best && oe < best_e)) {
+                    best = ob;
+                    best_e = oe;
+                }
+            }
+            if (best_e < 0) break;
+            last = best;
+            e_sel = best_e;
+        }
+        const int y = e_sel / k;
+        const int fl = isnew[e_sel];
+        int found = -1;
+        for (int r = lane; r < k; r += 32)
+            if (sid[r] == y) found = r;
+        for (int o = 16; o > 0; o >>= 1) found = max(found, __shfl_xor_sync(0xffffffffu, found, o));
+        if (lane == 0) {
+            if (found >= 0) {
+                if (fl) sfl[found] = 1;
+            } else {
+                sid[d] = y;
+                sfl[d] = fl;
+            }
+        }
+        if (found < 0) ++d;
+        __syncwarp();
+    }
+    for (int r = lane; r < d; r += 32) {
+        U[(int64_t)x * Ucap + r] = sid[r];
+        Uf[(int64_t)x * Ucap + r] = (uint8_t)sfl[r];
+    }
+    if (lane == 0) Udeg[x] = d;
+}
+
+__device__ __forceinline__ int sh_insert(int32_t *h, int hmask, int32_t v) {
+    uint32_t s = ((uint32_t)v * 2654435761u) & (uint32_t)hmask;
+    for (int probe = 0; probe <= hmask; ++probe) {
+        int32_t prev = atomicCAS(&h[s], -1, v);
+        if (prev == -1) return 1;
+        if (prev == v) return 0;
+        s = (s + 1) & (uint32_t)hmask;
+    }
+    return -1;
+}
+
+// candidates of x: v in U(U(x)), v > x, not in x's list, reached by a new edge
+__global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *Uf, const int32_t *Udeg,
+                      const int32_t *ids, int hsize, int lcap, int32_t *cand, int64_t cap,
+                      unsigned long long *counter, unsigned long long *cnt) {
+    extern __shared__ int32_t sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (x >= n) return;
+    int32_t *h = sm + wib * (hsize + lcap + 1);
+    int32_t *list = h + hsize;
+    int32_t *wcount = list + lcap;
+    for (int s = lane; s < hsize; s += 32) h[s] = -1;
+    if (lane == 0) *wcount = 0;
+    __syncwarp();
+    for (int r = lane; r < k; r += 32) sh_insert(h, hsize - 1, ids[(int64_t)x * k + r]);
+    __syncwarp();
+    const int degx = Udeg[x];
+    bool overflow = false;
+    for (int a = 0; a < degx; ++a) {
+        const int j = U[(int64_t)x * Ucap + a];
+        const int fxj = Uf[(int64_t)x * Ucap + a];
+        const int degj = Udeg[j];
+        for (int b = lane; b < degj; b += 32) {
+            const int v = U[(int64_t)j * Ucap + b];
+            const int fjv = Uf[(int64_t)j * Ucap + b];
+            if (v > x && (fxj | fjv)) {
+                int r = sh_insert(h, hsize - 1, v);
+                if (r == 1) {
+                    int pos = atomicAdd(wcount, 1);
+                    if (pos < lcap) list[pos] = v;
+                    else overflow = true;
+                } else if (r < 0)
+                    overflow = true;
+            }
+        }
+    }
+    __syncwarp();
+    int count = min(*wcount, lcap);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)count);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)base + count > cap) {
+        overflow = true;
+        count = (int64_t)base >= cap ? 0 : (int)(cap - (int64_t)base);
+    }
+    for (int q = lane; q < count; q += 32) {
+        cand[2 * (base + q)] = x;
+        cand[2 * (base + q) + 1] = list[q];
+    }
+    if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_OVERFLOW);
+}
+
+// offer each scored candidate to both endpoints if it beats their worst entry
+__global__ void k_offer(int64_t P, const int32_t *cand, const float *dc, int k, const float *knn_d,
+                        int32_t *ot, int32_t *ov, float *od, unsigned long long *counter, int64_t cap,
+                        unsigned long long *cnt) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const int x = cand[2 * q], v = cand[2 * q + 1];
+    const float d = dc[q];
+    const bool to_x = d < knn_d[(int64_t)x * k + k - 1];
+    const bool to_v = d < knn_d[(int64_t)v * k + k - 1];
+    int nn = (int)to_x + (int)to_v;
+    if (!nn) return;
+    unsigned long long pos = atomicAdd(counter, (unsigned long long)nn);
+    if ((int64_t)(pos + nn) > cap) {
+        atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_OVERFLOW);
+        return;
+    }
+    if (to_x) {
+        ot[pos] = x;
+        ov[pos] = v;
+        od[pos] = d;
+        ++pos;
+    }
+    if (to_v) {
+        ot[pos] = v;
+        ov[pos] = x;
+        od[pos] = d;
+    }
+}
+
+__global__ void k_count_targets(int64_t P, const int32_t *ot, int32_t *cntv) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < P) atomicAdd(&cntv[ot[q]], 1);
+}
+
+__global__ void k_scatter_offers(int64_t P, const int32_t *ot, const int32_t *ov, const float *od,
+                                 const int64_t *off, int32_t *cursor, int32_t *sv, float *sd) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const int x = ot[q];
+    const int pos = atomicAdd(&cursor[x], 1);
+    sv[off[x] + pos] = ov[q];
+    sd[off[x] + pos] = od[q];
+}
+
+// best k of (old list u offers) per node; old entries win ties
+__global__ void k_merge(int n, int k, const int32_t *gid, int32_t *ids, float *dd, uint8_t *isnew,
+                        const int64_t *off, const int32_t *sv, const float *sd, unsigned long long *delta) {
+    const int lane = threadIdx.x & 31;
+    const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (x >= n) return;
+    int id = -1;
+    float d = INFINITY;
+    uint32_t rk = 0xffffffffu;
+    if (lane < k) {
+        id = ids[(int64_t)x * k + lane];
+        d = dd[(int64_t)x * k + lane];
+        rk = 0;
+    }
+    const int gx = gid[x];
+    for (int64_t q = off[x]; q < off[x + 1]; ++q) {
+        const int v = sv[q];
+        const float dv = sd[q];
+        if (__any_sync(0xffffffffu, id == v)) continue;
+        const uint32_t rv = 1u + (uint32_t)(mix64(pair_key(gx, gid[v])) >> 33);
+        const float dw = __shfl_sync(0xffffffffu, d, k - 1);
+        const uint32_t rw = __shfl_sync(0xffffffffu, rk, k - 1);
+        if (!key_less(dv, rv, dw, rw)) continue;
+        const unsigned lt = __ballot_sync(0xffffffffu, lane < k && key_less(d, rk, dv, rv));
+        const int pos = __popc(lt);
+        const int id_up = __shfl_up_sync(0xffffffffu, id, 1);
+        const float d_up = __shfl_up_sync(0xffffffffu, d, 1);
+        const uint32_t rk_up = __shfl_up_sync(0xffffffffu, rk, 1);
+        if (lane > pos && lane < k) {
+            id = id_up;
+            d = d_up;
+            rk = rk_up;
+        }
+        if (lane == pos) {
+            id = v;
+            d = dv;
+            rk = rv;
+        }
+    }
+    if (lane < k) {
+        ids[(int64_t)x * k + lane] = id;
+        dd[(int64_t)x * k + lane] = d;
+        isnew[(int64_t)x * k + lane] = rk != 0;
+    }
+    const int nnew = __popc(__ballot_sync(0xffffffffu, lane < k && rk != 0));
+    if (lane == 0 && nnew) atomicAdd(delta, (unsigned long long)nnew);
+}
+
+// D+ selection keys: (d, hash of the unordered pair); equal pairs stay adjacent
+__global__ void k_edge_keys(int n, int k, const int32_t *gid, const int32_t *ids, const float *dd,
+                            unsigned long long *keys, uint32_t *vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * k) return;
+    const int x = (int)(e / k), y = ids[e];
+    const uint32_t hsh = (uint32_t)(mix64(pair_key(gid[x], gid[y])) >> 32);
+    keys[e] = ((unsigned long long)float_key(dd[e]) << 32) | hsh;
+    vals[e] = (uint32_t)e;
+}
+
+// D = unique undirected pairs of D+ (set insertion), written as global pairs
+__global__ void k_take_D(int64_t nDp, int k, const int32_t *gid, const int32_t *ids, const float *dd,
+                         const uint32_t *sorted_e, unsigned long long *dset, uint64_t dmask, int32_t *Dp,
+                         float *Dd, unsigned long long *counter, unsigned long long *cnt) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nDp) return;
+    const uint32_t e = sorted_e[q];
+    const int x = (int)(e / (uint32_t)k), y = ids[e];
+    const int a = gid[x], b = gid[y];
+    const int r = set_insert(dset, dmask, pair_key(a, b));
+    if (r < 0) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
+    if (r != 1) return;
+    unsigned long long pos = atomicAdd(counter, 1ull);
+    Dp[2 * pos] = a < b ? a : b;
+    Dp[2 * pos + 1] = a < b ? b : a;
+    Dd[pos] = dd[e];
+}
+
+// saturated nodes: every out-edge in D
+__global__ void k_saturated(int n, int k, const int32_t *gid, const int32_t *ids, const unsigned long long *dset,
+                            uint64_t dmask, int64_t *flag) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    bool all = true;
+    for (int r = 0; r < k && all; ++r)
+        all = set_contains(dset, dmask, pair_key(gid[x], gid[ids[(int64_t)x * k + r]]));
+    flag[x] = all ? 1 : 0;
+}
+
+__global__ void k_compact_nodes(int n, const int64_t *flag, const int64_t *pos, const int32_t *gid, int32_t *out) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n && flag[x]) out[pos[x]] = gid[x];
+}
+
+// all pairs x < y of a node set of size n, lexicographic
+__device__ __forceinline__ void tri_unrank(int64_t e, int64_t n, int &x, int &y) {
+    // rows x hold n-1-x pairs; row start s(x) = x(2n - x - 1)/2
+    double nn = (double)n;
+    double disc = (2 * nn - 1) * (2 * nn - 1) - 8.0 * (double)e;
+    int64_t xx = (int64_t)floor(((2 * nn - 1) - sqrt(fmax(disc, 0.0))) / 2);
+    if (xx < 0) xx = 0;
+    if (xx > n - 2) xx = n - 2;
+    auto start = [&](int64_t r) { return r * (2 * n - r - 1) / 2; };
+    while (xx > 0 && start(xx) > e) --xx;
+    while (xx < n - 2 && start(xx + 1) <= e) ++xx;
+    x = (int)xx;
+    y = (int)(e - start(xx) + xx + 1);
+}
+
+__global__ void k_all_pairs(int64_t n, int64_t np, int32_t *pairs) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    int x, y;
+    tri_unrank(e, n, x, y);
+    pairs[2 * e] = x;
+    pairs[2 * e + 1] = y;
+}
+
+// keys (d, lexicographic rank): ascending order is (d, i, j)
+__global__ void k_rank_keys(int64_t np, const float *dd, unsigned long long *keys, uint32_t *vals) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= np) return;
+    keys[e] = ((unsigned long long)float_key(dd[e]) << 32) | (uint32_t)e;
+    vals[e] = (uint32_t)e;
+}
+
+__global__ void k_gather_pairs(int64_t m, const uint32_t *sel, const int32_t *pairs_local, const int32_t *gid,
+                               const float *dd, int32_t *outp, float *outd) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const uint32_t e = sel[q];
+    int a = pairs_local[2 * (int64_t)e], b = pairs_local[2 * (int64_t)e + 1];
+    if (gid) {
+        a = gid[a];
+        b = gid[b];
+    }
+    outp[2 * q] = a < b ? a : b;
+    outp[2 * q + 1] = a < b ? b : a;
+    outd[q] = dd[e];
+}
+
+// dense symmetric d matrix of a node set (diagonal +inf) from all-pairs scores
+__global__ void k_dense_fill(int64_t n, int64_t np, const int32_t *pairs, const float *dd, float *Dm) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) Dm[e * n + e] = INFINITY;
+    if (e >= np) return;
+    const int x = pairs[2 * e], y = pairs[2 * e + 1];
+    Dm[(int64_t)x * n + y] = dd[e];
+    Dm[(int64_t)y * n + x] = dd[e];
+}
+
+// exact k smallest of each row by (d, column): radix select on the float key,
+// then an ordered gather; one block per row
+__global__ void __launch_bounds__(256) k_row_topk(int64_t n, int k, const float *Dm, int32_t *ids, float *dd) {
+    __shared__ int hist[256];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_rem;
+    __shared__ int scan[257];
+    const int64_t x = blockIdx.x;
+    const float *row = Dm + x * n;
+    uint32_t prefix = 0;
+    int rem = k;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        hist[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t hmask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
+        for (int64_t y = threadIdx.x; y < n; y += blockDim.x) {
+            uint32_t kk = float_key(row[y]);
+            if ((kk & hmask) == (prefix & hmask)) atomicAdd(&hist[(kk >> shift) & 0xff], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0, dsel = 255;
+            for (int dg = 0; dg < 256; ++dg) {
+                if (acc + hist[dg] >= rem) {
+                    dsel = dg;
+                    break;
+                }
+                acc += hist[dg];
+            }
+            s_prefix = prefix | ((uint32_t)dsel << shift);
+            s_rem = rem - acc;
+        }
+        __syncthreads();
+        prefix = s_prefix;
+        rem = s_rem;
+        __syncthreads();
+    }
+    // prefix = key of the k-th smallest; take all keys < prefix and the first
+    // `rem` keys == prefix in column order
+    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t y0 = threadIdx.x * chunk, y1 = min(n, y0 + chunk);
+    int nl = 0, ne = 0;
+    for (int64_t y = y0; y < y1; ++y) {
+        uint32_t kk = float_key(row[y]);
+        nl += kk < prefix;
+        ne += kk == prefix;
+    }
+    // exclusive scans of nl and ne (two passes through `scan`)
+    scan[threadIdx.x + 1] = nl;
+    if (threadIdx.x == 0) scan[0] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 1; t <= (int)blockDim.x; ++t) scan[t] += scan[t - 1];
+    __syncthreads();
+    int base_l = scan[threadIdx.x];
+    __syncthreads();
+    scan[threadIdx.x + 1] = ne;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 1; t <= (int)blockDim.x; ++t) scan[t] += scan[t - 1];
+    __syncthreads();
+    int base_e = scan[threadIdx.x];
+    const int n_less = k - rem;
+    int pl = base_l, pe = base_e;
+    for (int64_t y = y0; y < y1; ++y) {
+        float v = row[y];
+        uint32_t kk = float_key(v);
+        int slot = -1;
+        if (kk < prefix)
+            slot = pl++;
+        else if (kk == prefix) {
+            if (pe < rem) slot = n_less + pe;
+            ++pe;
+        }
+        if (slot >= 0 && slot < k) {
+            ids[x * k + slot] = (int32_t)y;
+            dd[x * k + slot] = v;
+        }
+    }
+}
+
+__global__ void k_pair_keys(int64_t P, const int32_t *pairs, unsigned long long *keys, uint32_t *vals) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    keys[q] = ((unsigned long long)(uint32_t)pairs[2 * q] << 32) | (uint32_t)pairs[2 * q + 1];
+    vals[q] = (uint32_t)q;
+}
+
+__global__ void k_d_keys(int64_t P, const uint32_t *perm, const float *dd, unsigned long long *keys,
+                         uint32_t *vals) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    keys[q] = float_key(dd[perm[q]]);
+    vals[q] = perm[q];
+}
+
+// first occurrence flags of equal pairs that are adjacent in `perm` order
+__global__ void k_unique_flags(int64_t P, const uint32_t *perm, const int32_t *pairs, int64_t *flag) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    bool first = true;
+    if (q > 0) {
+        uint32_t a = perm[q], b = perm[q - 1];
+        first = !(pairs[2 * (int64_t)a] == pairs[2 * (int64_t)b] && pairs[2 * (int64_t)a + 1] == pairs[2 * (int64_t)b + 1]);
+    }
+    flag[q] = first ? 1 : 0;
+}
+
+__global__ void k_unique_gather(int64_t P, int64_t m, const uint32_t *perm, const int64_t *flag,
+                                const int64_t *pos, const int32_t *pairs, const float *dd, int32_t *outp,
+                                float *outd) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P || !flag[q] || pos[q] >= m) return;
+    const uint32_t a = perm[q];
+    outp[2 * pos[q]] = pairs[2 * (int64_t)a];
+    outp[2 * pos[q] + 1] = pairs[2 * (int64_t)a + 1];
+    outd[pos[q]] = dd[a];
+}
+
+__global__ void k_iota(int32_t *p, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) p[e] = (int32_t)e;
+}
+
+inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+#define CKS(call)                                                \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);   \
+    } while (0)
+
+static bool grow(recon_ctx *c, DBuf &b, size_t bytes) {
+    if (b.bytes >= bytes) return true;
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 256);
+    want = want + want / 4;
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", want);
+        return false;
+    }
+    b.bytes = want;
+    return true;
+}
+// grows b to at least `bytes`, keeping its first `keep` bytes
+static bool grow_keep(recon_ctx *c, DBuf &b, size_t bytes, size_t keep) {
+    if (b.bytes >= bytes) return true;
+    size_t want = std::max<size_t>(bytes, 256);
+    want = want + want / 2;
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", want);
+        return false;
+    }
+    if (b.p) {
+        if (keep) cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(b.p);
+    }
+    b.p = p;
+    b.bytes = want;
+    return true;
+}
+#define GROW_KEEP(buf, bytes, keep)                                   \
+    do {                                                              \
+        if (!grow_keep(c, (buf), (bytes), (keep))) return RECON_ENOMEM; \
+    } while (0)
+
+#define GROW(buf, bytes)                                   \
+    do {                                                   \
+        if (!grow(c, (buf), (bytes))) return RECON_ENOMEM; \
+    } while (0)
+
+void free_search_bufs(SearchBufs *sb) {
+    if (!sb) return;
+    for (DBuf *b : sb->all())
+        if (b->p) cudaFree(b->p);
+    delete sb;
+}
+
+static SearchBufs &SB(recon_ctx *c) {
+    if (!c->sb) c->sb = new SearchBufs();
+    return *c->sb;
+}
+
+static unsigned long long *counter(recon_ctx *c, int slot) { return c->cnt + slot; }
+
+static recon_status read_counter(recon_ctx *c, int slot, unsigned long long *out) {
+    CKS(cudaMemcpyAsync(c->cnt_host + slot, c->cnt + slot, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream));
+    CKS(cudaStreamSynchronize(c->stream));
+    *out = c->cnt_host[slot];
+    return RECON_OK;
+}
+
+static recon_status check_err_flags(recon_ctx *c, const char *where) {
+    unsigned long long f = 0;
+    recon_status st = read_counter(c, CNT_ERR, &f);
+    if (st != RECON_OK) return st;
+    if (f) {
+        CKS(cudaMemsetAsync(c->cnt + CNT_ERR, 0, sizeof(unsigned long long), c->stream));
+        if (f & ERR_OVERFLOW) return set_err(c, RECON_ENOMEM, "%s: a search buffer overflowed", where);
+        if (f & ERR_TABLE_FULL) return set_err(c, RECON_ENOMEM, "%s: a hash table is full", where);
+        return set_err(c, RECON_EINVAL, "%s: device-side check failed (flags %llx)", where, f);
+    }
+    return RECON_OK;
+}
+
+// score `P` pairs (local ids through gid, or global when gid == NULL) into d
+recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, const int32_t *gid, float *d,
+                                float *w) {
+    if (P <= 0) return RECON_OK;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (c->opt.timing) {
+        for (cudaEvent_t *ev : {&ea, &eb}) {
+            if (!c->event_pool.empty()) {
+                *ev = c->event_pool.back();
+                c->event_pool.pop_back();
+            } else
+                CKS(cudaEventCreate(ev));
+        }
+        CKS(cudaEventRecord(ea, c->stream));
+    }
+    cudaError_t e;
+    if (c->model == RECON_ISING)
+        e = launch_ising_score(c->iv(), c->W, c->sp(), pairs, P, gid, d, w, c->cnt, c->stream);
+    else
+        e = launch_gauss_score(c->gv(), c->W, c->sp(), pairs, P, gid, d, w, c->cnt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "score kernel");
+    if (c->opt.timing) {
+        CKS(cudaEventRecord(eb, c->stream));
+        c->timed.push_back({ea, eb, P});
+    }
+    c->stats.pair_evals += P;
+    return RECON_OK;
+}
+
+// sort (key, val) pairs; the sorted result is left in (keys, vals)
+static recon_status sort_kv(recon_ctx *c, unsigned long long *keys, uint32_t *vals, int64_t n, int bit0,
+                            int bit1) {
+    SearchBufs &S = SB(c);
+    GROW(S.sort_k2, sizeof(unsigned long long) * std::max<int64_t>(n, 1));
+    GROW(S.sort_v2, sizeof(uint32_t) * std::max<int64_t>(n, 1));
+    GROW(S.sort_tmp, sizeof(int64_t) * radix_tmp_elems(std::max<int64_t>(n, 1)));
+    bool alt = false;
+    CKS(radix_sort_u64(keys, vals, (unsigned long long *)S.sort_k2.p, (uint32_t *)S.sort_v2.p, n, bit0, bit1,
+                       (int64_t *)S.sort_tmp.p, &alt, c->stream));
+    if (alt) {
+        CKS(cudaMemcpyAsync(keys, S.sort_k2.p, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, c->stream));
+        CKS(cudaMemcpyAsync(vals, S.sort_v2.p, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return RECON_OK;
+}
+
+// m best pairs among all pairs of the node set gid[0..n) (gid NULL: all nodes);
+// appends them (global ids) to the result list
+static recon_status exhaustive_best_set(recon_ctx *c, const int32_t *gid, int64_t n, int64_t m) {
+    SearchBufs &S = SB(c);
+    const int64_t np = n * (n - 1) / 2;
+    if (np <= 0 || m <= 0) return RECON_OK;
+    if (np >= ((int64_t)1 << 32)) return set_err(c, RECON_EUNSUPPORTED, "exhaustive search over %lld nodes", (long long)n);
+    GROW(S.ex_pairs, sizeof(int32_t) * 2 * np);
+    GROW(S.ex_d, sizeof(float) * np);
+    GROW(S.ex_keys, sizeof(unsigned long long) * np);
+    GROW(S.ex_vals, sizeof(uint32_t) * np);
+    k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p); note_launch();
+    CKS(cudaGetLastError());
+    recon_status st = score_pairs_device(c, (int32_t *)S.ex_pairs.p, np, gid, (float *)S.ex_d.p, nullptr);
+    if (st != RECON_OK) return st;
+    k_rank_keys<<<nblk(np), 256, 0, c->stream>>>(np, (float *)S.ex_d.p, (unsigned long long *)S.ex_keys.p,
+                                                 (uint32_t *)S.ex_vals.p); note_launch();
+    CKS(cudaGetLastError());
+    st = sort_kv(c, (unsigned long long *)S.ex_keys.p, (uint32_t *)S.ex_vals.p, np, 0, 64);
+    if (st != RECON_OK) return st;
+    const int64_t take = std::min(m, np);
+    GROW_KEEP(S.res_pairs, sizeof(int32_t) * 2 * (S.res_n + take), sizeof(int32_t) * 2 * S.res_n);
+    GROW_KEEP(S.res_d, sizeof(float) * (S.res_n + take), sizeof(float) * S.res_n);
+    k_gather_pairs<<<nblk(take), 256, 0, c->stream>>>(take, (uint32_t *)S.ex_vals.p, (int32_t *)S.ex_pairs.p, gid,
+                                                      (float *)S.ex_d.p, (int32_t *)S.res_pairs.p + 2 * S.res_n,
+                                                      (float *)S.res_d.p + S.res_n); note_launch();
+    CKS(cudaGetLastError());
+    S.res_n += take;
+    return RECON_OK;
+}
+
+// exact KNN of a node set: all pairs scored once, then the k smallest per row
+static recon_status knn_exhaustive(recon_ctx *c, const int32_t *gid, int n, int k) {
+    SearchBufs &S = SB(c);
+    const int64_t np = (int64_t)n * (n - 1) / 2;
+    GROW(S.ex_pairs, sizeof(int32_t) * 2 * np);
+    GROW(S.ex_d, sizeof(float) * np);
+    GROW(S.dense, sizeof(float) * (size_t)n * n);
+    k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p); note_launch();
+    CKS(cudaGetLastError());
+    recon_status st = score_pairs_device(c, (int32_t *)S.ex_pairs.p, np, gid, (float *)S.ex_d.p, nullptr);
+    if (st != RECON_OK) return st;
+    k_dense_fill<<<nblk(std::max<int64_t>(np, n)), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p,
+                                                                           (float *)S.ex_d.p, (float *)S.dense.p); note_launch();
+    CKS(cudaGetLastError());
+    k_row_topk<<<n, 256, 0, c->stream>>>(n, k, (float *)S.dense.p, (int32_t *)S.knn_id.p, (float *)S.knn_d.p); note_launch();
+    CKS(cudaGetLastError());
+    return RECON_OK;
+}
+
+// NNDescent on the node set gid[0..n) with lists of k; returns iterations
+static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k, uint64_t seed, int *iters_out) {
+    SearchBufs &S = SB(c);
+    const int64_t nk = (int64_t)n * k;
+    const int in_cap = k, Ucap = k + in_cap;
+    GROW(S.pairs_tmp, sizeof(int32_t) * 2 * nk);
+    // 1. random initial lists, scored
+    k_knn_init<<<nblk(n), 256, 0, c->stream>>>(n, k, seed, (int32_t *)S.knn_id.p); note_launch();
+    CKS(cudaGetLastError());
+    k_list_pairs<<<nblk(nk), 256, 0, c->stream>>>(n, k, (int32_t *)S.knn_id.p, (int32_t *)S.pairs_tmp.p); note_launch();
+    CKS(cudaGetLastError());
+    recon_status st = score_pairs_device(c, (int32_t *)S.pairs_tmp.p, nk, gid, (float *)S.knn_d.p, nullptr);
+    if (st != RECON_OK) return st;
+    k_sort_lists<<<nblk(n), 128, 0, c->stream>>>(n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
+                                                 (uint8_t *)S.knn_new.p); note_launch();
+    CKS(cudaGetLastError());
+
+    GROW(S.indeg, sizeof(int32_t) * (n + 1));
+    GROW(S.inoff, sizeof(int64_t) * (n + 1));
+    GROW(S.cursor, sizeof(int32_t) * (n + 1));
+    GROW(S.in_e, sizeof(int32_t) * nk);
+    GROW(S.U, sizeof(int32_t) * (size_t)n * Ucap);
+    GROW(S.Uf, sizeof(uint8_t) * (size_t)n * Ucap);
+    GROW(S.Udeg, sizeof(int32_t) * n);
+    GROW(S.scan_in, sizeof(int64_t) * (n + 1));
+    GROW(S.scan_tmp, sizeof(int64_t) * scan_tmp_elems(n + 1));
+    const int raw = Ucap * Ucap;
+    int hsize = 1;
+    while (hsize < 2 * (raw + k)) hsize <<= 1;
+    const int lcap = raw;
+    const size_t per_warp = sizeof(int32_t) * (size_t)(hsize + lcap + 1);
+    int warps_per_block = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
+    const size_t smem_gen = per_warp * warps_per_block;
+    if (smem_gen > 48 * 1024)
+        CKS(cudaFuncSetAttribute(k_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gen));
+    // node x has at most min(raw, n-1-x) candidates
+    const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * raw, (int64_t)n * (n - 1) / 2), 1);
+    GROW(S.cand, sizeof(int32_t) * 2 * cand_cap);
+    GROW(S.cand_d, sizeof(float) * cand_cap);
+
+    int max_iters = c->opt.max_knn_iters;
+    if (max_iters <= 0) max_iters = 2 * (int)std::ceil(std::log((double)std::max(n, 2)) / std::log(2.0 * k)) + 2;
+    int it = 0;
+    for (it = 0; it < max_iters;) {
+        ++it;
+        const uint64_t seed_it = mix64(seed ^ (0x5bd1e995ull * (uint64_t)it));
+        // 2. U
+        CKS(cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), c->stream));
+        k_in_count<<<nblk(nk), 256, 0, c->stream>>>(nk, (int32_t *)S.knn_id.p, (int32_t *)S.indeg.p); note_launch();
+        CKS(cudaGetLastError());
+        k_i32_to_i64<<<nblk(n + 1), 256, 0, c->stream>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1); note_launch();
+        CKS(cudaGetLastError());
+        CKS(launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p, c->stream));
+        CKS(cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), c->stream));
+        k_in_fill<<<nblk(nk), 256, 0, c->stream>>>(nk, (int32_t *)S.knn_id.p, (int64_t *)S.inoff.p,
+                                                   (int32_t *)S.cursor.p, (int32_t *)S.in_e.p); note_launch();
+        CKS(cudaGetLastError());
+        {
+            const int wpb = 8;
+            size_t smem = sizeof(int32_t) * 2 * Ucap * wpb;
+            k_build_U<<<nblk((int64_t)n * 32, 32 * wpb), 32 * wpb, smem, c->stream>>>(
+                n, k, in_cap, Ucap, seed_it, (int32_t *)S.knn_id.p, (uint8_t *)S.knn_new.p, (int64_t *)S.inoff.p,
+                (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
+                (int32_t *)S.Udeg.p); note_launch();
+            CKS(cudaGetLastError());
+        }
+        // 3. candidates
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
+        k_gen<<<nblk((int64_t)n * 32, 32 * warps_per_block), 32 * warps_per_block, smem_gen, c->stream>>>(
+            n, k, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p, (int32_t *)S.knn_id.p, hsize, lcap,
+            (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt); note_launch();
+        CKS(cudaGetLastError());
+        unsigned long long ncand = 0;
+        st = read_counter(c, CNT_SCRATCH0, &ncand);
+        if (st != RECON_OK) return st;
+        if ((int64_t)ncand > cand_cap) ncand = cand_cap;
+        // 4. score and offer
+        st = score_pairs_device(c, (int32_t *)S.cand.p, (int64_t)ncand, gid, (float *)S.cand_d.p, nullptr);
+        if (st != RECON_OK) return st;
+        const int64_t ocap = 2 * std::max<int64_t>((int64_t)ncand, 1);
+        GROW(S.off_t, sizeof(int32_t) * ocap);
+        GROW(S.off_v, sizeof(int32_t) * ocap);
+        GROW(S.off_d, sizeof(float) * ocap);
+        GROW(S.off_sv, sizeof(int32_t) * ocap);
+        GROW(S.off_sd, sizeof(float) * ocap);
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH1), 0, sizeof(unsigned long long), c->stream));
+        k_offer<<<nblk((int64_t)ncand), 256, 0, c->stream>>>((int64_t)ncand, (int32_t *)S.cand.p,
+                                                             (float *)S.cand_d.p, k, (float *)S.knn_d.p,
+                                                             (int32_t *)S.off_t.p, (int32_t *)S.off_v.p,
+                                                             (float *)S.off_d.p, counter(c, CNT_SCRATCH1), ocap,
+                                                             c->cnt); note_launch();
+        CKS(cudaGetLastError());
+        unsigned long long noff = 0;
+        st = read_counter(c, CNT_SCRATCH1, &noff);
+        if (st != RECON_OK) return st;
+        if ((int64_t)noff > ocap) noff = ocap;
+        // group offers by target
+        CKS(cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), c->stream));
+        k_count_targets<<<nblk((int64_t)noff), 256, 0, c->stream>>>((int64_t)noff, (int32_t *)S.off_t.p,
+                                                                    (int32_t *)S.indeg.p); note_launch();
+        CKS(cudaGetLastError());
+        k_i32_to_i64<<<nblk(n + 1), 256, 0, c->stream>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1); note_launch();
+        CKS(cudaGetLastError());
+        CKS(launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p, c->stream));
+        CKS(cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), c->stream));
+        k_scatter_offers<<<nblk((int64_t)noff), 256, 0, c->stream>>>(
+            (int64_t)noff, (int32_t *)S.off_t.p, (int32_t *)S.off_v.p, (float *)S.off_d.p, (int64_t *)S.inoff.p,
+            (int32_t *)S.cursor.p, (int32_t *)S.off_sv.p, (float *)S.off_sd.p); note_launch();
+        CKS(cudaGetLastError());
+        // 5. merge
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH2), 0, sizeof(unsigned long long), c->stream));
+        k_merge<<<nblk((int64_t)n * 32), 256, 0, c->stream>>>(n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
+                                                               (uint8_t *)S.knn_new.p, (int64_t *)S.inoff.p,
+                                                               (int32_t *)S.off_sv.p, (float *)S.off_sd.p,
+                                                               counter(c, CNT_SCRATCH2)); note_launch();
+        CKS(cudaGetLastError());
+        unsigned long long delta = 0;
+        st = read_counter(c, CNT_SCRATCH2, &delta);
+        if (st != RECON_OK) return st;
+        st = check_err_flags(c, "NNDescent");
+        if (st != RECON_OK) return st;
+        if ((double)delta / ((double)k * n) < c->opt.eps_knn) break;
+    }
+    *iters_out = it;
+    return RECON_OK;
+}
+
+// final m best of the collected (global) pairs, ordered by (d, i, j), unique
+static recon_status finish_results(recon_ctx *c, int64_t m, int64_t *count) {
+    SearchBufs &S = SB(c);
+    const int64_t P = S.res_n;
+    *count = 0;
+    if (P == 0) return RECON_OK;
+    GROW(S.fk, sizeof(unsigned long long) * P);
+    GROW(S.fv, sizeof(uint32_t) * P);
+    GROW(S.flag, sizeof(int64_t) * P);
+    GROW(S.pos, sizeof(int64_t) * P);
+    GROW(S.scan_tmp2, sizeof(int64_t) * scan_tmp_elems(P));
+    GROW(S.out_pairs, sizeof(int32_t) * 2 * std::max<int64_t>(m, 1));
+    GROW(S.out_d, sizeof(float) * std::max<int64_t>(m, 1));
+    k_pair_keys<<<nblk(P), 256, 0, c->stream>>>(P, (int32_t *)S.res_pairs.p, (unsigned long long *)S.fk.p,
+                                                (uint32_t *)S.fv.p); note_launch();
+    CKS(cudaGetLastError());
+    recon_status st = sort_kv(c, (unsigned long long *)S.fk.p, (uint32_t *)S.fv.p, P, 0, 64);
+    if (st != RECON_OK) return st;
+    GROW(S.fk2, sizeof(unsigned long long) * P);
+    GROW(S.fv2, sizeof(uint32_t) * P);
+    k_d_keys<<<nblk(P), 256, 0, c->stream>>>(P, (uint32_t *)S.fv.p, (float *)S.res_d.p, (unsigned long long *)S.fk2.p,
+                                             (uint32_t *)S.fv2.p); note_launch();
+    CKS(cudaGetLastError());
+    st = sort_kv(c, (unsigned long long *)S.fk2.p, (uint32_t *)S.fv2.p, P, 0, 32);
+    if (st != RECON_OK) return st;
+    k_unique_flags<<<nblk(P), 256, 0, c->stream>>>(P, (uint32_t *)S.fv2.p, (int32_t *)S.res_pairs.p,
+                                                   (int64_t *)S.flag.p); note_launch();
+    CKS(cudaGetLastError());
+    CKS(launch_scan_i64((int64_t *)S.flag.p, (int64_t *)S.pos.p, P, (int64_t *)S.scan_tmp2.p, c->stream));
+    k_unique_gather<<<nblk(P), 256, 0, c->stream>>>(P, m, (uint32_t *)S.fv2.p, (int64_t *)S.flag.p,
+                                                    (int64_t *)S.pos.p, (int32_t *)S.res_pairs.p, (float *)S.res_d.p,
+                                                    (int32_t *)S.out_pairs.p, (float *)S.out_d.p); note_launch();
+    CKS(cudaGetLastError());
+    int64_t last_pos = 0, last_flag = 0;
+    CKS(cudaMemcpyAsync(&last_pos, (int64_t *)S.pos.p + P - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CKS(cudaMemcpyAsync(&last_flag, (int64_t *)S.flag.p + P - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CKS(cudaStreamSynchronize(c->stream));
+    *count = std::min(m, last_pos + last_flag);
+    return RECON_OK;
+}
+
+recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count) {
+    SearchBufs &S = SB(c);
+    S.res_n = 0;
+    c->stats.levels = 0;
+    c->stats.knn_iters = 0;
+    for (int t = 0; t < 16; ++t) c->stats.level_k[t] = 0;
+    for (int t = 0; t < 17; ++t) c->stats.level_size[t] = 0;
+    const int64_t N = c->N;
+    GROW(S.gid_a, sizeof(int32_t) * N);
+    GROW(S.gid_b, sizeof(int32_t) * N);
+    k_iota<<<nblk(N), 256, 0, c->stream>>>((int32_t *)S.gid_a.p, N); note_launch();
+    CKS(cudaGetLastError());
+    int32_t *gid = (int32_t *)S.gid_a.p, *gid_next = (int32_t *)S.gid_b.p;
+    int64_t n = N;
+    const uint64_t call_seed = mix64(c->opt.seed ^ mix64(0x9e37ull + (uint64_t)c->stats_calls));
+    c->stats_calls++;
+    for (int level = 0;; ++level) {
+        if (level < 17) c->stats.level_size[level] = n;
+        if (n * n <= 4 * m) {
+            recon_status st = exhaustive_best_set(c, level == 0 ? nullptr : gid, n, m);
+            if (st != RECON_OK) return st;
+            break;
+        }
+        int64_t k64 = (4 * m + n - 1) / n;
+        k64 = std::max<int64_t>(k64, k_cfg);
+        k64 = std::min<int64_t>(k64, n - 1);
+        const int k = (int)k64;
+        if (level < 16) c->stats.level_k[level] = k;
+        c->stats.levels = level + 1;
+        const int64_t nk = n * k;
+        GROW(S.knn_id, sizeof(int32_t) * nk);
+        GROW(S.knn_d, sizeof(float) * nk);
+        GROW(S.knn_new, sizeof(uint8_t) * nk);
+        bool exhaustive = c->opt.knn_mode == RECON_KNN_EXHAUSTIVE || k > NND_MAX_K;
+        if (c->opt.knn_mode == RECON_KNN_AUTO) {
+            // NNDescent scores about |S| (2k)^2 / 2 pairs per iteration
+            double nnd = (double)n * 4.0 * k * k / 2.0 * 3.0;
+            double exh = (double)n * (n - 1) / 2.0;
+            exhaustive = exhaustive || exh <= nnd;
+        }
+        if (exhaustive && (double)n * n * 4.0 > 16e9)
+            return set_err(c, RECON_EUNSUPPORTED, "level of %lld nodes with k = %d needs NNDescent with k <= %d",
+                           (long long)n, k, NND_MAX_K);
+        recon_status st;
+        if (exhaustive) {
+            st = knn_exhaustive(c, gid, (int)n, k);
+        } else {
+            int iters = 0;
+            st = knn_nndescent(c, gid, (int)n, k, mix64(call_seed + (uint64_t)level), &iters);
+            c->stats.knn_iters += iters;
+        }
+        if (st != RECON_OK) return st;
+        // D+ : the 2m best directed edges
+        GROW(S.ek, sizeof(unsigned long long) * nk);
+        GROW(S.ev, sizeof(uint32_t) * nk);
+        k_edge_keys<<<nblk(nk), 256, 0, c->stream>>>((int)n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
+                                                     (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p); note_launch();
+        CKS(cudaGetLastError());
+        st = sort_kv(c, (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p, nk, 0, 64);
+        if (st != RECON_OK) return st;
+        const int64_t nDp = std::min<int64_t>(2 * m, nk);
+        // D : unique pairs of D+
+        uint64_t dcap = 1;
+        while (dcap < (uint64_t)(4 * nDp + 64)) dcap <<= 1;
+        GROW(S.dset, sizeof(unsigned long long) * dcap);
+        CKS(launch_fill_u64((unsigned long long *)S.dset.p, RECON_EMPTY_KEY, (int64_t)dcap, c->stream));
+        GROW_KEEP(S.res_pairs, sizeof(int32_t) * 2 * (S.res_n + nDp), sizeof(int32_t) * 2 * S.res_n);
+        GROW_KEEP(S.res_d, sizeof(float) * (S.res_n + nDp), sizeof(float) * S.res_n);
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH3), 0, sizeof(unsigned long long), c->stream));
+        k_take_D<<<nblk(nDp), 256, 0, c->stream>>>(nDp, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
+                                                   (uint32_t *)S.ev.p, (unsigned long long *)S.dset.p, dcap - 1,
+                                                   (int32_t *)S.res_pairs.p + 2 * S.res_n,
+                                                   (float *)S.res_d.p + S.res_n, counter(c, CNT_SCRATCH3), c->cnt); note_launch();
+        CKS(cudaGetLastError());
+        unsigned long long nD = 0;
+        st = read_counter(c, CNT_SCRATCH3, &nD);
+        if (st != RECON_OK) return st;
+        S.res_n += (int64_t)nD;
+        // S' : saturated nodes
+        GROW(S.flag, sizeof(int64_t) * (n + 1));
+        GROW(S.pos, sizeof(int64_t) * (n + 1));
+        GROW(S.scan_tmp2, sizeof(int64_t) * scan_tmp_elems(n + 1));
+        k_saturated<<<nblk(n), 256, 0, c->stream>>>((int)n, k, gid, (int32_t *)S.knn_id.p,
+                                                    (unsigned long long *)S.dset.p, dcap - 1, (int64_t *)S.flag.p); note_launch();
+        CKS(cudaGetLastError());
+        CKS(cudaMemsetAsync((int64_t *)S.flag.p + n, 0, sizeof(int64_t), c->stream));
+        CKS(launch_scan_i64((int64_t *)S.flag.p, (int64_t *)S.pos.p, n + 1, (int64_t *)S.scan_tmp2.p, c->stream));
+        k_compact_nodes<<<nblk(n), 256, 0, c->stream>>>((int)n, (int64_t *)S.flag.p, (int64_t *)S.pos.p, gid,
+                                                        gid_next); note_launch();
+        CKS(cudaGetLastError());
+        int64_t n2 = 0;
+        CKS(cudaMemcpyAsync(&n2, (int64_t *)S.pos.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+        CKS(cudaStreamSynchronize(c->stream));
+        st = check_err_flags(c, "FindBest");
+        if (st != RECON_OK) return st;
+        std::swap(gid, gid_next);
+        n = n2;
+        if (n < 2) {
+            if (level + 1 < 17) c->stats.level_size[level + 1] = n;
+            break;
+        }
+    }
+    recon_status st = finish_results(c, m, count);
+    if (st != RECON_OK) return st;
+    *pairs_dev = (int32_t *)S.out_pairs.p;
+    *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}
+
+recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count) {
+    SearchBufs &S = SB(c);
+    S.res_n = 0;
+    recon_status st = exhaustive_best_set(c, nullptr, c->N, m);
+    if (st != RECON_OK) return st;
+    st = finish_results(c, m, count);
+    if (st != RECON_OK) return st;
+    *pairs_dev = (int32_t *)S.out_pairs.p;
+    *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}

@@ -1,0 +1,40 @@
+// search.cuh -- scratch buffers of the best-pairs search (internal).
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct SearchBufs {
+    DBuf knn_id, knn_d, knn_new;                  // lists of the current level
+    DBuf indeg, inoff, cursor, in_e;              // reverse edges
+    DBuf U, Uf, Udeg;                             // undirected view
+    DBuf scan_in, scan_tmp, scan_tmp2;            // scans
+    DBuf cand, cand_d;                            // candidate pairs and scores
+    DBuf off_t, off_v, off_d, off_sv, off_sd;     // offers
+    DBuf pairs_tmp;                               // scratch pair list
+    DBuf ek, ev;                                  // edge sort
+    DBuf dset;                                    // D membership set
+    DBuf flag, pos;                               // compaction
+    DBuf gid_a, gid_b;                            // level node sets
+    DBuf ex_pairs, ex_d, ex_keys, ex_vals, dense;  // exhaustive scoring
+    DBuf res_pairs, res_d;                        // collected pairs
+    DBuf fk, fv, fk2, fv2;                        // final ordering
+    DBuf out_pairs, out_d;                        // result
+    DBuf sort_k2, sort_v2, sort_tmp;              // radix sort scratch
+    int64_t res_n = 0;
+
+    std::vector<DBuf *> all() {
+        return {&knn_id, &knn_d, &knn_new, &indeg, &inoff, &cursor, &in_e, &U, &Uf, &Udeg,
+                &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &off_t, &off_v, &off_d, &off_sv,
+                &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
+                &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
+                &out_d, &sort_k2, &sort_v2, &sort_tmp};
+    }
+};
+
+void free_search_bufs(SearchBufs *sb);
+recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, const int32_t *gid, float *d,
+                                float *w);
+recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
+recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);

@@ -1,0 +1,306 @@
+"""ctypes binding of librecon (include/recon.h): the same entry points under
+the same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts NumPy arrays
+and torch tensors to pointers and status codes to exceptions.  There is no
+fallback: if ``librecon.so`` is missing or no GPU is usable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librecon.so")
+
+RECON_OK, RECON_EINVAL, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT, RECON_ESTATE, RECON_EUNSUPPORTED = range(7)
+RECON_ISING, RECON_GAUSSIAN = 0, 1
+RECON_X_INT8, RECON_X_FP32 = 0, 1
+RECON_KNN_NNDESCENT, RECON_KNN_EXHAUSTIVE, RECON_KNN_AUTO = 0, 1, 2
+RECON_SEED_RANDOM, RECON_SEED_SCREEN, RECON_SEED_LEARNED = 0, 1, 2
+STATUS_NAMES = ["RECON_OK", "RECON_EINVAL", "RECON_ENOMEM", "RECON_ECUDA", "RECON_ETIMEOUT", "RECON_ESTATE",
+                "RECON_EUNSUPPORTED"]
+
+
+class recon_options(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("seed", C.c_uint64), ("eps_knn", C.c_double),
+                ("max_knn_iters", C.c_int32), ("w_clamp", C.c_float), ("h_clamp", C.c_float),
+                ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
+                ("timing", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class recon_stats(C.Structure):
+    _fields_ = [("pair_evals", C.c_int64), ("newton_passes", C.c_int64), ("knn_iters", C.c_int64),
+                ("levels", C.c_int32), ("level_k", C.c_int32 * 16), ("level_size", C.c_int64 * 17),
+                ("nnz", C.c_int64), ("samples", C.c_int64), ("kernel_launches", C.c_int64),
+                ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double)]
+
+
+class ReconError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+
+
+_lib = None
+_EXPORTS = {
+    "recon_default_options": (None, [C.c_void_p]),
+    "recon_init": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                             C.c_void_p, C.c_void_p]),
+    "recon_objective": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "recon_score": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]),
+    "recon_best_pairs": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_int64,
+                                   C.c_void_p, C.c_int32]),
+    "recon_exhaustive_best": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                        C.c_int32]),
+    "recon_cd_sweep": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "recon_field_sweep": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "recon_gcd_step": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "recon_get_model": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "recon_set_model": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "recon_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "recon_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "recon_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
+    "recon_last_error": (C.c_char_p, [C.c_void_p]),
+    "recon_destroy": (None, [C.c_void_p]),
+}
+
+
+def lib():
+    """Loads librecon.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != RECON_OK:
+        msg = lib().recon_last_error(ctx)
+        raise ReconError(st, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, is_device, keepalive) of a NumPy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        assert x.is_contiguous()
+        return x.data_ptr(), int(x.is_cuda), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data, 0, a
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def recon_default_options(**kw) -> recon_options:
+    o = recon_options()
+    lib().recon_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, "lambda_" if k in ("lam", "lambda") else k, v)
+    return o
+
+
+def recon_init(X, model: int = RECON_ISING, options: recon_options | None = None, stream=None):
+    """X: samples, sample-major (M x N): int8 spins (Ising) or float32 (Gaussian);
+    a NumPy array or a (host or CUDA) torch tensor.  Returns a context handle."""
+    if _is_torch(X):
+        M, N = X.shape
+        xt = RECON_X_INT8 if str(X.dtype) == "torch.int8" else RECON_X_FP32
+    else:
+        X = np.ascontiguousarray(X)
+        M, N = X.shape
+        xt = RECON_X_INT8 if X.dtype == np.int8 else RECON_X_FP32
+    p, dev, keep = _ptr(X)
+    ctx = C.c_void_p()
+    opt = options if options is not None else recon_default_options()
+    st = lib().recon_init(C.byref(ctx), p, M, N, xt, dev, model, C.byref(opt), _stream_handle(stream))
+    _check(st, None)
+    return ctx
+
+
+def recon_objective(ctx) -> float:
+    out = C.c_double()
+    _check(lib().recon_objective(ctx, C.byref(out)), ctx)
+    return out.value
+
+
+def recon_score(ctx, pairs, d_out=None, w_out=None):
+    """d(i,j) = -gain for each pair.  Host arrays in -> host arrays out; CUDA
+    tensors in -> the given CUDA output tensors are filled."""
+    if _is_torch(pairs) and pairs.is_cuda:
+        P = pairs.shape[0]
+        _check(lib().recon_score(ctx, pairs.data_ptr(), P, d_out.data_ptr(),
+                                 w_out.data_ptr() if w_out is not None else None, 1), ctx)
+        return d_out, w_out
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = len(pairs)
+    d = np.empty(P, dtype=np.float32)
+    w = np.empty(P, dtype=np.float32)
+    _check(lib().recon_score(ctx, pairs.ctypes.data, P, d.ctypes.data, w.ctypes.data, 0), ctx)
+    return d, w
+
+
+def recon_best_pairs(ctx, k: int, kappa: float, N: int):
+    m = int(np.floor(kappa * N + 0.5))
+    cap = max(min(m, N * (N - 1) // 2), 1)
+    pairs = np.empty((cap, 2), dtype=np.int32)
+    d = np.empty(cap, dtype=np.float32)
+    mo = C.c_int64()
+    _check(lib().recon_best_pairs(ctx, k, float(kappa), pairs.ctypes.data, d.ctypes.data, cap, C.byref(mo), 0), ctx)
+    return pairs[:mo.value], d[:mo.value]
+
+
+def recon_exhaustive_best(ctx, m: int, N: int):
+    cap = max(min(m, N * (N - 1) // 2), 1)
+    pairs = np.empty((cap, 2), dtype=np.int32)
+    d = np.empty(cap, dtype=np.float32)
+    mo = C.c_int64()
+    _check(lib().recon_exhaustive_best(ctx, m, pairs.ctypes.data, d.ctypes.data, cap, C.byref(mo), 0), ctx)
+    return pairs[:mo.value], d[:mo.value]
+
+
+def recon_cd_sweep(ctx, pairs) -> float:
+    p, dev, keep = _ptr(pairs if _is_torch(pairs) else np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = pairs.shape[0] if _is_torch(pairs) else keep.shape[0]
+    out = C.c_double()
+    _check(lib().recon_cd_sweep(ctx, p, P, dev, C.byref(out)), ctx)
+    return out.value
+
+
+def recon_field_sweep(ctx) -> float:
+    out = C.c_double()
+    _check(lib().recon_field_sweep(ctx, C.byref(out)), ctx)
+    return out.value
+
+
+def recon_gcd_step(ctx, k: int, kappa: float):
+    dl, ob, m = C.c_double(), C.c_double(), C.c_int64()
+    _check(lib().recon_gcd_step(ctx, k, float(kappa), C.byref(dl), C.byref(ob), C.byref(m)), ctx)
+    return dl.value, ob.value, m.value
+
+
+def recon_get_model(ctx, N: int):
+    nnz = C.c_int64()
+    fields = np.empty(N, dtype=np.float32)
+    st = lib().recon_get_model(ctx, None, None, 0, C.byref(nnz), fields.ctypes.data)
+    if st not in (RECON_OK, RECON_EINVAL):
+        _check(st, ctx)
+    n = nnz.value
+    ij = np.empty((max(n, 1), 2), dtype=np.int32)
+    w = np.empty(max(n, 1), dtype=np.float32)
+    _check(lib().recon_get_model(ctx, ij.ctypes.data, w.ctypes.data, n, C.byref(nnz), fields.ctypes.data), ctx)
+    return ij[:n], w[:n], fields
+
+
+def recon_set_model(ctx, ij, w, fields=None):
+    ij = np.ascontiguousarray(np.asarray(ij, dtype=np.int32).reshape(-1, 2))
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float32))
+    f = None if fields is None else np.ascontiguousarray(np.asarray(fields, dtype=np.float32))
+    _check(lib().recon_set_model(ctx, ij.ctypes.data, w.ctypes.data, len(w), None if f is None else f.ctypes.data),
+           ctx)
+
+
+def recon_get_stats(ctx) -> dict:
+    s = recon_stats()
+    _check(lib().recon_get_stats(ctx, C.byref(s)), ctx)
+    return {"pair_evals": s.pair_evals, "newton_passes": s.newton_passes, "knn_iters": s.knn_iters,
+            "levels": s.levels, "level_k": list(s.level_k[:max(s.levels, 0)]),
+            "level_size": list(s.level_size[:max(s.levels, 0) + 1]), "nnz": s.nnz, "samples": s.samples,
+            "kernel_launches": s.kernel_launches, "score_launches": s.score_launches,
+            "score_pairs": s.score_pairs, "score_ms": s.score_ms}
+
+
+def recon_save(ctx, path: str):
+    _check(lib().recon_save(ctx, path.encode()), ctx)
+
+
+def recon_load(path: str, stream=None):
+    ctx = C.c_void_p()
+    _check(lib().recon_load(C.byref(ctx), path.encode(), _stream_handle(stream)), None)
+    return ctx
+
+
+def recon_last_error(ctx=None) -> str:
+    m = lib().recon_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def recon_destroy(ctx):
+    if ctx:
+        lib().recon_destroy(ctx)
+
+
+class Recon:
+    """Owning wrapper around a context."""
+
+    def __init__(self, X, model: int = RECON_ISING, stream=None, **options):
+        X_shape = tuple(X.shape)
+        self.M, self.N = X_shape
+        self.model = model
+        self.ctx = recon_init(X, model, recon_default_options(**options), stream)
+
+    def close(self):
+        if self.ctx:
+            recon_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def objective(self):
+        return recon_objective(self.ctx)
+
+    def score(self, pairs, d_out=None, w_out=None):
+        return recon_score(self.ctx, pairs, d_out, w_out)
+
+    def best_pairs(self, k: int, kappa: float):
+        return recon_best_pairs(self.ctx, k, kappa, self.N)
+
+    def exhaustive_best(self, m: int):
+        return recon_exhaustive_best(self.ctx, m, self.N)
+
+    def cd_sweep(self, pairs):
+        return recon_cd_sweep(self.ctx, pairs)
+
+    def field_sweep(self):
+        return recon_field_sweep(self.ctx)
+
+    def gcd_step(self, k: int, kappa: float):
+        return recon_gcd_step(self.ctx, k, kappa)
+
+    def get_model(self):
+        return recon_get_model(self.ctx, self.N)
+
+    def set_model(self, ij, w, fields=None):
+        return recon_set_model(self.ctx, ij, w, fields)
+
+    def stats(self):
+        return recon_get_stats(self.ctx)
+
+    def save(self, path):
+        recon_save(self.ctx, path)
