@@ -664,7 +664,15 @@ extern "C" recon_status recon_get_stats(recon_ctx *c, recon_stats *out) {
 // ---------------------------------------------------------------------------
 // checkpoints
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'E', 'C', 'O', 'N', 'C', 'K', '1'};
+static const char kMagic[8] = {'R', 'E', 'C', 'O', 'N', 'C', 'K', '2'};
+
+// the tracked per-sample state, saved as is so that a resumed run continues
+// bit for bit: Ising phi, t and H; Gaussian mu and e
+static std::vector<std::pair<float *, size_t>> state_arrays(recon_ctx *c) {
+    const size_t rows = (size_t)c->N * c->Mp;
+    if (c->model == RECON_ISING) return {{c->phi, rows}, {c->t, rows}, {c->H, (size_t)c->N}};
+    return {{c->mu, rows}, {c->e, rows}, {c->Q, (size_t)c->N}};
+}
 
 extern "C" recon_status recon_save(recon_ctx *c, const char *path) {
     LIVE(c);
@@ -689,6 +697,15 @@ extern "C" recon_status recon_save(recon_ctx *c, const char *path) {
               fwrite(fields.data(), sizeof(float), c->N, f) == (size_t)c->N &&
               (nnz == 0 || (fwrite(ij.data(), sizeof(int32_t), 2 * nnz, f) == (size_t)(2 * nnz) &&
                             fwrite(w.data(), sizeof(float), nnz, f) == (size_t)nnz));
+    for (auto &a : state_arrays(c)) {
+        if (!ok) break;
+        std::vector<float> hbuf(a.second);
+        if (cudaMemcpy(hbuf.data(), a.first, sizeof(float) * a.second, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            return cuda_fail(c, cudaGetLastError(), "checkpoint read-back");
+        }
+        ok = fwrite(hbuf.data(), sizeof(float), a.second, f) == a.second;
+    }
     ok = (fclose(f) == 0) && ok;
     if (!ok) return set_err(c, RECON_EINVAL, "write to %s failed", path);
     return RECON_OK;
@@ -720,6 +737,10 @@ extern "C" recon_status recon_load(recon_ctx **out, const char *path, void *stre
     ok = fread(X.data(), 1, X.size(), f) == X.size() && fread(fields.data(), sizeof(float), N, f) == (size_t)N &&
          (nnz == 0 || (fread(ij.data(), sizeof(int32_t), 2 * nnz, f) == (size_t)(2 * nnz) &&
                        fread(w.data(), sizeof(float), nnz, f) == (size_t)nnz));
+    const size_t rows = (size_t)N * ((M + 31) / 32 * 32);
+    std::vector<float> s_a(rows), s_b(rows), s_c(N);
+    ok = ok && fread(s_a.data(), sizeof(float), rows, f) == rows && fread(s_b.data(), sizeof(float), rows, f) == rows &&
+         fread(s_c.data(), sizeof(float), N, f) == (size_t)N;
     fclose(f);
     if (!ok) return set_err(nullptr, RECON_EINVAL, "%s is truncated", path);
     // w_clamp was stored resolved; it is valid input as is
@@ -732,6 +753,12 @@ extern "C" recon_status recon_load(recon_ctx **out, const char *path, void *stre
         g_err = c->err;
         recon_destroy(c);
         return st;
+    }
+    {
+        auto arr = state_arrays(c);
+        const float *src[3] = {s_a.data(), s_b.data(), s_c.data()};
+        for (int q = 0; q < 3; ++q)
+            CK(cudaMemcpyAsync(arr[q].first, src[q], sizeof(float) * arr[q].second, cudaMemcpyHostToDevice, c->stream));
     }
     CK(cudaMemcpyAsync(c->cnt + CNT_NEWTON, &s.newton_passes, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));

@@ -262,6 +262,10 @@ cudaError_t launch_ising_objective(IsingView v, double *partials, int nblocks, c
 cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
                                const int32_t *gid, float *d_out, float *w_out,
                                unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+                                   const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
+                                   int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out,
+                                   unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
                                 unsigned long long *cnt, cudaStream_t s);

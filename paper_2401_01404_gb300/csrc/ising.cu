@@ -154,14 +154,13 @@ __device__ __forceinline__ float pass_gain(const RS &R, float delta, float tau) 
     return warp_sum(q);
 }
 
-// The whole 1-D problem for one pair (all lanes of the warp participate and
-// end with identical results).
+// The 1-D problem of one pair once its pass at delta = 0 is known (sums of u
+// and v over the samples and the count of disagreeing spins).  All lanes of the
+// warp take part and end with identical results.
 template <class RS>
-__device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, float W0, float lambda,
-                                           float wclamp, float &gain, float &wstar, int &passes) {
-    float su, sv;
-    int dis;
-    pass0(R, su, sv, dis);
+__device__ __forceinline__ void solve_from_pass0(const RS &R, int Mp, float su, float sv, int dis, float Hsum,
+                                                 float W0, float lambda, float wclamp, float &gain, float &wstar,
+                                                 int &passes) {
     const float twoA = 2.f * (float)(Mp - 2 * dis);
     const float D0 = twoA - su - sv;  // F'(0)
     passes = 0;
@@ -216,6 +215,64 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
     }
     gain = fmaxf(g, 0.f);
     wstar = w;
+}
+
+template <class RS>
+__device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, float W0, float lambda,
+                                           float wclamp, float &gain, float &wstar, int &passes) {
+    float su, sv;
+    int dis;
+    pass0(R, su, sv, dis);
+    solve_from_pass0(R, Mp, su, sv, dis, Hsum, W0, lambda, wclamp, gain, wstar, passes);
+}
+
+// Row i staged in shared memory (t and the sign bits), row j streamed.
+struct SmemRows {
+    static constexpr int kNW = 0;
+    const float *st;     // t_i, shared
+    const uint32_t *sb;  // x_i sign bits, shared
+    const float *Tj;
+    const uint32_t *Bj;
+    int Mw, lane;
+    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb_) const {
+        a = st[32 * c + lane];
+        b = __ldg(Tj + 32 * c + lane);
+        sa = (sb[c] << (31 - lane)) & 0x80000000u;
+        sb_ = (__ldg(Bj + c) << (31 - lane)) & 0x80000000u;
+    }
+};
+
+// pass 0 against a staged row: sv = sum x_i t_j (x_i as +-1 floats in shared
+// memory), su = sum x_j t_i (sign of t_i flipped by x_j's bit), and the count of
+// disagreeing spins by popcount of whole words.  Four words in flight per lane.
+__device__ __forceinline__ void pass0_staged(const float *st, const float *sx, const uint32_t *sb, const float *Tj,
+                                             const uint32_t *Bj, int Mw, int lane, float &su, float &sv, int &dis) {
+    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+    int c = 0;
+    for (; c + 4 <= Mw; c += 4) {
+        float t0 = __ldg(Tj + 32 * c + lane), t1 = __ldg(Tj + 32 * (c + 1) + lane);
+        float t2 = __ldg(Tj + 32 * (c + 2) + lane), t3 = __ldg(Tj + 32 * (c + 3) + lane);
+        uint32_t w0 = __ldg(Bj + c), w1 = __ldg(Bj + c + 1), w2 = __ldg(Bj + c + 2), w3 = __ldg(Bj + c + 3);
+        b0 = fmaf(sx[32 * c + lane], t0, b0);
+        b1 = fmaf(sx[32 * (c + 1) + lane], t1, b1);
+        b0 = fmaf(sx[32 * (c + 2) + lane], t2, b0);
+        b1 = fmaf(sx[32 * (c + 3) + lane], t3, b1);
+        a0 += flip(st[32 * c + lane], (w0 << (31 - lane)) & 0x80000000u);
+        a1 += flip(st[32 * (c + 1) + lane], (w1 << (31 - lane)) & 0x80000000u);
+        a0 += flip(st[32 * (c + 2) + lane], (w2 << (31 - lane)) & 0x80000000u);
+        a1 += flip(st[32 * (c + 3) + lane], (w3 << (31 - lane)) & 0x80000000u);
+    }
+    for (; c < Mw; ++c) {
+        float t0 = __ldg(Tj + 32 * c + lane);
+        uint32_t w0 = __ldg(Bj + c);
+        b0 = fmaf(sx[32 * c + lane], t0, b0);
+        a0 += flip(st[32 * c + lane], (w0 << (31 - lane)) & 0x80000000u);
+    }
+    int d = 0;
+    for (int q = lane; q < Mw; q += 32) d += __popc(sb[q] ^ __ldg(Bj + q));
+    su = warp_sum(a0 + a1);
+    sv = warp_sum(b0 + b1);
+    dis = warp_sum_i(d);
 }
 
 // ---------------------------------------------------------------------------
@@ -334,6 +391,61 @@ __global__ void k_objective(IsingView v, double *partials) {
         r = warp_sum_d(r);
         if (threadIdx.x == 0) partials[blockIdx.x] = r;
     }
+}
+
+// Candidates grouped by their first node (one block per segment): segment s
+// covers node x = seg_node[s] (local id) and candidates at output positions
+// seg_start[s] .. + seg_count[s]; the second node of candidate q is
+// cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
+// in shared memory once; each warp streams the rows of its candidates.
+__global__ void __launch_bounds__(256) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+                                                   const int64_t *seg_start, const int32_t *seg_count,
+                                                   const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
+                                                   const int32_t *gid, float *d_out, unsigned long long *cnt) {
+    extern __shared__ float sm[];
+    const int64_t sidx = blockIdx.x;
+    if (sidx >= nseg) return;
+    const int count = seg_count[sidx];
+    if (count <= 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *st = sm;
+    float *sx = sm + v.Mp;
+    uint32_t *sb = (uint32_t *)(sm + 2 * v.Mp);
+    const int x = seg_node[sidx];
+    const int gx = gid ? gid[x] : x;
+    const float *Tx = v.t + (int64_t)gx * v.Mp;
+    const uint32_t *Bx = v.xbits + (int64_t)gx * v.Mw;
+    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) {
+        st[m] = Tx[m];
+        sx[m] = ((Bx[m >> 5] >> (m & 31)) & 1u) ? -1.f : 1.f;
+    }
+    for (int c = threadIdx.x; c < v.Mw; c += blockDim.x) sb[c] = Bx[c];
+    __syncthreads();
+    const float Hx = v.H[gx];
+    const int64_t start = seg_start[sidx];
+    const int vbase = seg_vbase ? seg_vbase[sidx] : 0;
+    unsigned long long npass = 0;
+    for (int q = warp; q < count; q += nw) {
+        const int64_t pos = start + q;
+        const int vl = cand ? cand[2 * pos + 1] : vbase + q;
+        const int gj = gid ? gid[vl] : vl;
+        const float W0 = wt_lookup(W, pair_key(gx, gj));
+        const float Hj = v.H[gj];
+        const float *Tj = v.t + (int64_t)gj * v.Mp;
+        const uint32_t *Bj = v.xbits + (int64_t)gj * v.Mw;
+        float su, sv;
+        int dis;
+        pass0_staged(st, sx, sb, Tj, Bj, v.Mw, lane, su, sv, dis);
+        SmemRows R{st, sb, Tj, Bj, v.Mw, lane};
+        float g, w;
+        int passes;
+        solve_from_pass0(R, v.Mp, su, sv, dis, Hx + Hj, W0, p.lambda, p.w_clamp, g, w, passes);
+        if (lane == 0) {
+            d_out[pos] = -g;
+            npass += (unsigned long long)passes;
+        }
+    }
+    if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
 }
 
 template <class RS>
@@ -557,7 +669,21 @@ cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32
     int64_t want = P;
     int64_t cap = (int64_t)1 << 20;  // warps; grid-stride beyond
     unsigned grid = grid_for(want < cap ? want : cap);
-    DISPATCH_ROWS(v.Mw, (k_score<RS><<<grid, 256, 0, s>>>(v, W, p, pairs, P, gid, d_out, w_out, cnt))); note_launch();
+    // most pairs stop after the first pass: stream both rows (low registers, high occupancy)
+    k_score<GlobRows><<<grid, 256, 0, s>>>(v, W, p, pairs, P, gid, d_out, w_out, cnt);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+                                   const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
+                                   int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out,
+                                   unsigned long long *cnt, cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    size_t smem = sizeof(float) * 2 * v.Mp + sizeof(uint32_t) * v.Mw;
+    k_score_seg<<<(unsigned)nseg, 256, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
+                                                  gid, d_out, cnt);
+    note_launch();
     return cudaGetLastError();
 }
 

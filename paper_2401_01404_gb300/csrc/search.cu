@@ -194,7 +194,8 @@ __device__ __forceinline__ int sh_insert(int32_t *h, int hmask, int32_t v) {
 // candidates of x: v in U(U(x)), v > x, not in x's list, reached by a new edge
 __global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *Uf, const int32_t *Udeg,
                       const int32_t *ids, int hsize, int lcap, int32_t *cand, int64_t cap,
-                      unsigned long long *counter, unsigned long long *cnt) {
+                      unsigned long long *counter, unsigned long long *cnt, int32_t *seg_node, int64_t *seg_start,
+                      int32_t *seg_count) {
     extern __shared__ int32_t sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -239,6 +240,11 @@ __global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *U
     for (int q = lane; q < count; q += 32) {
         cand[2 * (base + q)] = x;
         cand[2 * (base + q) + 1] = list[q];
+    }
+    if (lane == 0) {
+        seg_node[x] = x;
+        seg_start[x] = (int64_t)base;
+        seg_count[x] = count;
     }
     if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_OVERFLOW);
 }
@@ -689,6 +695,84 @@ recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, c
     return RECON_OK;
 }
 
+// score grouped candidates (see k_score_seg); the Gaussian model scores the
+// pair list directly
+recon_status score_segments_device(recon_ctx *c, const int32_t *seg_node, const int64_t *seg_start,
+                                   const int32_t *seg_count, const int32_t *seg_vbase, int64_t nseg,
+                                   const int32_t *cand, int64_t P, const int32_t *gid, float *d) {
+    if (P <= 0) return RECON_OK;
+    if (c->model != RECON_ISING) return score_pairs_device(c, cand, P, gid, d, nullptr);
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (c->opt.timing) {
+        for (cudaEvent_t *ev : {&ea, &eb}) {
+            if (!c->event_pool.empty()) {
+                *ev = c->event_pool.back();
+                c->event_pool.pop_back();
+            } else
+                CKS(cudaEventCreate(ev));
+        }
+        CKS(cudaEventRecord(ea, c->stream));
+    }
+    cudaError_t e = launch_ising_score_seg(c->iv(), c->W, c->sp(), seg_node, seg_start, seg_count, seg_vbase, nseg,
+                                           cand, gid, d, c->cnt, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "segmented score kernel");
+    if (c->opt.timing) {
+        CKS(cudaEventRecord(eb, c->stream));
+        c->timed.push_back({ea, eb, P});
+    }
+    c->stats.pair_evals += P;
+    return RECON_OK;
+}
+
+// all pairs x < y of n nodes as segments of at most 512 candidates each, in
+// lexicographic output order
+static recon_status all_pair_segments(recon_ctx *c, int64_t n, int64_t *nseg_out) {
+    SearchBufs &S = SB(c);
+    std::vector<int32_t> node, cntv, vb;
+    std::vector<int64_t> start;
+    int64_t pos = 0;
+    for (int64_t x = 0; x + 1 < n; ++x) {
+        for (int64_t y0 = x + 1; y0 < n; y0 += 512) {
+            int64_t cc = std::min<int64_t>(512, n - y0);
+            node.push_back((int32_t)x);
+            start.push_back(pos);
+            cntv.push_back((int32_t)cc);
+            vb.push_back((int32_t)y0);
+            pos += cc;
+        }
+    }
+    const int64_t ns = (int64_t)node.size();
+    GROW(S.seg_node, sizeof(int32_t) * std::max<int64_t>(ns, 1));
+    GROW(S.seg_start, sizeof(int64_t) * std::max<int64_t>(ns, 1));
+    GROW(S.seg_count, sizeof(int32_t) * std::max<int64_t>(ns, 1));
+    GROW(S.seg_vbase, sizeof(int32_t) * std::max<int64_t>(ns, 1));
+    if (ns) {
+        CKS(cudaMemcpyAsync(S.seg_node.p, node.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
+        CKS(cudaMemcpyAsync(S.seg_start.p, start.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, c->stream));
+        CKS(cudaMemcpyAsync(S.seg_count.p, cntv.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
+        CKS(cudaMemcpyAsync(S.seg_vbase.p, vb.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, c->stream));
+        CKS(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    }
+    *nseg_out = ns;
+    return RECON_OK;
+}
+
+// scores every pair x < y of the node set (local ids; gid maps them) into d,
+// in lexicographic order; pairs (local) are written too
+static recon_status score_all_pairs(recon_ctx *c, const int32_t *gid, int64_t n, int32_t *pairs, float *d) {
+    SearchBufs &S = SB(c);
+    const int64_t np = n * (n - 1) / 2;
+    k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, pairs);
+    note_launch();
+    CKS(cudaGetLastError());
+    if (c->model != RECON_ISING) return score_pairs_device(c, pairs, np, gid, d, nullptr);
+    int64_t ns = 0;
+    recon_status st = all_pair_segments(c, n, &ns);
+    if (st != RECON_OK) return st;
+    return score_segments_device(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p,
+                                 (int32_t *)S.seg_vbase.p, ns, nullptr, np, gid, d);
+}
+
 // sort (key, val) pairs; the sorted result is left in (keys, vals)
 static recon_status sort_kv(recon_ctx *c, unsigned long long *keys, uint32_t *vals, int64_t n, int bit0,
                             int bit1) {
@@ -717,9 +801,7 @@ static recon_status exhaustive_best_set(recon_ctx *c, const int32_t *gid, int64_
     GROW(S.ex_d, sizeof(float) * np);
     GROW(S.ex_keys, sizeof(unsigned long long) * np);
     GROW(S.ex_vals, sizeof(uint32_t) * np);
-    k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p); note_launch();
-    CKS(cudaGetLastError());
-    recon_status st = score_pairs_device(c, (int32_t *)S.ex_pairs.p, np, gid, (float *)S.ex_d.p, nullptr);
+    recon_status st = score_all_pairs(c, gid, n, (int32_t *)S.ex_pairs.p, (float *)S.ex_d.p);
     if (st != RECON_OK) return st;
     k_rank_keys<<<nblk(np), 256, 0, c->stream>>>(np, (float *)S.ex_d.p, (unsigned long long *)S.ex_keys.p,
                                                  (uint32_t *)S.ex_vals.p); note_launch();
@@ -744,9 +826,7 @@ static recon_status knn_exhaustive(recon_ctx *c, const int32_t *gid, int n, int 
     GROW(S.ex_pairs, sizeof(int32_t) * 2 * np);
     GROW(S.ex_d, sizeof(float) * np);
     GROW(S.dense, sizeof(float) * (size_t)n * n);
-    k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p); note_launch();
-    CKS(cudaGetLastError());
-    recon_status st = score_pairs_device(c, (int32_t *)S.ex_pairs.p, np, gid, (float *)S.ex_d.p, nullptr);
+    recon_status st = score_all_pairs(c, gid, n, (int32_t *)S.ex_pairs.p, (float *)S.ex_d.p);
     if (st != RECON_OK) return st;
     k_dense_fill<<<nblk(std::max<int64_t>(np, n)), 256, 0, c->stream>>>(n, np, (int32_t *)S.ex_pairs.p,
                                                                            (float *)S.ex_d.p, (float *)S.dense.p); note_launch();
@@ -795,6 +875,9 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * raw, (int64_t)n * (n - 1) / 2), 1);
     GROW(S.cand, sizeof(int32_t) * 2 * cand_cap);
     GROW(S.cand_d, sizeof(float) * cand_cap);
+    GROW(S.seg_node, sizeof(int32_t) * n);
+    GROW(S.seg_start, sizeof(int64_t) * n);
+    GROW(S.seg_count, sizeof(int32_t) * n);
 
     int max_iters = c->opt.max_knn_iters;
     if (max_iters <= 0) max_iters = 2 * (int)std::ceil(std::log((double)std::max(n, 2)) / std::log(2.0 * k)) + 2;
@@ -826,14 +909,16 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
         CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
         k_gen<<<nblk((int64_t)n * 32, 32 * warps_per_block), 32 * warps_per_block, smem_gen, c->stream>>>(
             n, k, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p, (int32_t *)S.knn_id.p, hsize, lcap,
-            (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt); note_launch();
+            (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt, (int32_t *)S.seg_node.p,
+            (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p); note_launch();
         CKS(cudaGetLastError());
         unsigned long long ncand = 0;
         st = read_counter(c, CNT_SCRATCH0, &ncand);
         if (st != RECON_OK) return st;
         if ((int64_t)ncand > cand_cap) ncand = cand_cap;
         // 4. score and offer
-        st = score_pairs_device(c, (int32_t *)S.cand.p, (int64_t)ncand, gid, (float *)S.cand_d.p, nullptr);
+        st = score_segments_device(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p,
+                                   nullptr, n, (int32_t *)S.cand.p, (int64_t)ncand, gid, (float *)S.cand_d.p);
         if (st != RECON_OK) return st;
         const int64_t ocap = 2 * std::max<int64_t>((int64_t)ncand, 1);
         GROW(S.off_t, sizeof(int32_t) * ocap);

@@ -11,6 +11,7 @@ struct SearchBufs {
     DBuf U, Uf, Udeg;                             // undirected view
     DBuf scan_in, scan_tmp, scan_tmp2;            // scans
     DBuf cand, cand_d;                            // candidate pairs and scores
+    DBuf seg_node, seg_start, seg_count, seg_vbase;  // candidates grouped by first node
     DBuf off_t, off_v, off_d, off_sv, off_sd;     // offers
     DBuf pairs_tmp;                               // scratch pair list
     DBuf ek, ev;                                  // edge sort
@@ -26,7 +27,7 @@ struct SearchBufs {
 
     std::vector<DBuf *> all() {
         return {&knn_id, &knn_d, &knn_new, &indeg, &inoff, &cursor, &in_e, &U, &Uf, &Udeg,
-                &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &off_t, &off_v, &off_d, &off_sv,
+                &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &seg_node, &seg_start, &seg_count, &seg_vbase, &off_t, &off_v, &off_d, &off_sv,
                 &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
                 &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
                 &out_d, &sort_k2, &sort_v2, &sort_tmp};
