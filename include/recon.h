@@ -155,6 +155,26 @@ recon_status recon_score(recon_ctx *ctx, const int32_t *pairs, int64_t P, float 
 recon_status recon_best_pairs(recon_ctx *ctx, int32_t k, double kappa, int32_t *pairs, float *d,
                               int64_t cap, int64_t *m_out, int32_t out_is_device);
 
+/* recon_score_noalloc -- recon_score for host pair lists that performs no
+ * device allocation (the paper has no counterpart: this is a deployment
+ * variant).  Meant for callers that may not allocate device memory while they
+ * run: a process sharing the GPU with PyTorch or JAX, whose caching allocators
+ * hold most of the memory, or a serving loop that forbids allocation after
+ * start-up.  recon_score stages host pairs and results in buffers it grows with
+ * cudaMalloc/cudaFree (and cudaFree waits for the whole device); this call
+ * stages them in one array of 1 MiB that the library reserves statically in
+ * device memory on every GPU that loads it, for the life of the process.
+ *   pairs : P x 2 int32 host array; d_out (and w_out, may be NULL): P floats on
+ *           the host.  Same values as recon_score on the same pairs.
+ *   P     : at most 65536 per call; larger P returns RECON_EINVAL (split the
+ *           list into several calls).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents; each call clears the words
+ * it needs zeroed.  Calls that overlap on the GPU (several host threads or
+ * streams) race on the array.  Synchronous. */
+recon_status recon_score_noalloc(recon_ctx *ctx, const int32_t *pairs, int64_t P, float *d_out, float *w_out);
+
 /* recon_exhaustive_best -- the m best pairs over all N(N-1)/2 pairs, exact
  * (Algorithm 3's exhaustive base case applied to the whole node set); the
  * ground truth that recall is measured against.  Arguments as in

@@ -51,6 +51,7 @@ _EXPORTS = {
                              C.c_void_p, C.c_void_p]),
     "recon_objective": (C.c_int, [C.c_void_p, C.c_void_p]),
     "recon_score": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]),
+    "recon_score_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "recon_best_pairs": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.c_void_p, C.c_int32]),
     "recon_exhaustive_best": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -159,6 +160,17 @@ def recon_score(ctx, pairs, d_out=None, w_out=None):
     d = np.empty(P, dtype=np.float32)
     w = np.empty(P, dtype=np.float32)
     _check(lib().recon_score(ctx, pairs.ctypes.data, P, d.ctypes.data, w.ctypes.data, 0), ctx)
+    return d, w
+
+
+def recon_score_noalloc(ctx, pairs):
+    """recon_score for a host pair list without any device allocation (at most
+    65536 pairs per call); returns host arrays (d, w)."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    P = len(pairs)
+    d = np.empty(P, dtype=np.float32)
+    w = np.empty(P, dtype=np.float32)
+    _check(lib().recon_score_noalloc(ctx, pairs.ctypes.data, P, d.ctypes.data, w.ctypes.data), ctx)
     return d, w
 
 
