@@ -61,7 +61,11 @@ typedef enum {
 typedef enum {
     RECON_KNN_NNDESCENT = 0,  /* FindKNN by NNDescent (Algorithm 4) at every level */
     RECON_KNN_EXHAUSTIVE = 1, /* FindKNN by scoring every pair of the level's node set */
-    RECON_KNN_AUTO = 2        /* exhaustive where it costs fewer pair evaluations */
+    RECON_KNN_AUTO = 2,       /* exhaustive where it costs fewer pair evaluations */
+    RECON_KNN_SCREEN = 3      /* Algorithm 3's exhaustive base case over all nodes, computed
+                                 exactly: the tensor-core gradient screen (App. B's gradient
+                                 as distance) keeps every pair that can have a nonzero gain,
+                                 and only those, plus the stored couplings, are scored */
 } recon_knn_mode;
 
 typedef enum {
@@ -98,6 +102,10 @@ typedef struct {
     int64_t score_launches;   /* pair-scoring launches timed (options.timing) */
     int64_t score_pairs;      /* pairs those launches scored */
     double score_ms;          /* their summed device time, from CUDA events */
+    int64_t screen_launches;  /* tensor-core screen launches timed (options.timing) */
+    double screen_ms;         /* their summed device time */
+    double screen_flop;       /* their algorithmic work: 2 x (128 x 128 tiles) x K per launch */
+    int64_t screen_survivors; /* pairs the screen passed on, summed */
 } recon_stats;
 
 /* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,

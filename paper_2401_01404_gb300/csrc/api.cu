@@ -247,7 +247,7 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     if (o.w_clamp < 0.f) return set_err(nullptr, RECON_EINVAL, "w_clamp must be >= 0");
     if (model == RECON_ISING && o.w_clamp > 8.f)
         return set_err(nullptr, RECON_EINVAL, "w_clamp above 8 is not supported for the Ising model");
-    if (o.knn_mode < 0 || o.knn_mode > 2) return set_err(nullptr, RECON_EINVAL, "unknown knn_mode");
+    if (o.knn_mode < 0 || o.knn_mode > 3) return set_err(nullptr, RECON_EINVAL, "unknown knn_mode");
     if (o.seed_mode != RECON_SEED_RANDOM) return set_err(nullptr, RECON_EUNSUPPORTED, "seed_mode not built");
     const int64_t Mp = (M + 31) / 32 * 32;
     if (model == RECON_ISING && Mp / 32 > ising_max_words())
@@ -650,9 +650,14 @@ extern "C" recon_status recon_get_stats(recon_ctx *c, recon_stats *out) {
     for (auto &t : c->timed) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, t.a, t.b));
-        c->stats.score_ms += ms;
-        c->stats.score_launches += 1;
-        c->stats.score_pairs += t.pairs;
+        if (t.pairs >= 0) {
+            c->stats.score_ms += ms;
+            c->stats.score_launches += 1;
+            c->stats.score_pairs += t.pairs;
+        } else {  // a screen launch; -pairs carries nothing, its work is in screen_flop
+            c->stats.screen_ms += ms;
+            c->stats.screen_launches += 1;
+        }
         c->event_pool.push_back(t.a);
         c->event_pool.push_back(t.b);
     }

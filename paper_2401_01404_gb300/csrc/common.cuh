@@ -99,6 +99,17 @@ __device__ __forceinline__ float wt_lookup(const WTable &T, uint64_t key) {
     return 0.f;
 }
 
+__device__ __forceinline__ bool wt_contains(const WTable &T, uint64_t key) {
+    uint64_t s = mix64(key) & T.mask;
+    for (uint64_t probe = 0; probe <= T.mask; ++probe) {
+        unsigned long long k = T.keys[s];
+        if (k == key) return true;
+        if (k == RECON_EMPTY_KEY) return false;
+        s = (s + 1) & T.mask;
+    }
+    return false;
+}
+
 // Inserts or overwrites; returns false when the table is full.
 __device__ __forceinline__ bool wt_upsert(const WTable &T, uint64_t key, float v) {
     uint64_t s = mix64(key) & T.mask;
@@ -310,6 +321,12 @@ int64_t radix_tmp_elems(int64_t n);
 cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
                            uint32_t *vals_alt, int64_t n, int bit0, int bit1, int64_t *tmp,
                            bool *result_in_alt, cudaStream_t s);
+
+// screen.cu
+cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1);
+float screen_rel_err(int model, int Mp);
+cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
+                          unsigned long long *count, float margin_scale, int *tiles_out);
 
 // host helpers (api.cu)
 recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...);

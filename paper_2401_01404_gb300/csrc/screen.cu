@@ -1,0 +1,399 @@
+// screen.cu -- the tensor-core gradient screen: every pair's gradient at
+// W_ij = 0 at once, as one dense contraction on the 5th-generation tensor cores
+// (tcgen05 MMA, TMA tile loads, TMEM accumulators), with a fused epilogue that
+// keeps only the pairs whose exact gain can be nonzero.
+//
+// Why it is exact.  Under the Laplace prior, a pair at W_ij = 0 has a nonzero
+// gain iff |F'(0)| > lambda (the subgradient condition at w = 0), where
+//   Ising:    F'(0) = g_ij = sum_m [r_i x_j + x_i r_j],  r = x - tanh(phi)
+//   Gaussian: a_ij = -sum_m [e_i x_j + x_i e_j],       e = x + s2 mu
+// i.e. G = [R | X] [X | R]^T, a product of two N x 2Mp matrices.  The screen
+// computes G with bf16 operands and f32 accumulation; its error is bounded per
+// pair (|dG_ij| <= 2^-8 (|R|_1,i + |R|_1,j) for the Ising model, whose spins
+// are exact in bf16, plus the accumulation error), so keeping every pair with
+// |G~_ij| > lambda - margin_ij loses none of the pairs with a nonzero gain.  The
+// survivors, and every stored coupling, are then scored exactly in FP32; the
+// m best of them are the exact m best pairs (the exhaustive base case of
+// Algorithm 3 over the whole node set).  The gradient as a cheap proxy for d is
+// the paper's own suggestion (App. B, "Gradient as distance").
+//
+// Kernel layout: a persistent grid; each CTA walks the upper-triangular 128x128
+// tiles of G.  Warp 4 issues TMA loads of 128x64 bf16 tiles (128-byte swizzle)
+// into a 4-stage ring, warp 5 issues tcgen05.mma (M=128, N=128, K=16) into one
+// of two TMEM accumulators of 128 columns, warps 0-3 drain the other
+// accumulator (tcgen05.ld, one TMEM lane = one row per thread) and append the
+// surviving pairs.  Every wait is bounded (1 s); on a timeout the kernel sets
+// an error word, lets its own copies land, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+constexpr uint32_t TMEM_COLS = 256;  // two accumulators of 128 f32 columns
+constexpr int THREADS = 192;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t par) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (1 s of wall time); false on timeout or when another role gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile int *abort) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_try(b, par)) {
+        if (*abort) return false;
+        if (gtimer() - t0 > 1000000000ull) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(const void *p) {
+    const uint64_t a = su32(p);
+    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+#define TMEM_LD32(r, taddr)                                                                                        \
+    asm volatile(                                                                                                  \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%" \
+        "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                              \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),    \
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),  \
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
+        : "r"(taddr))
+
+// tile t of the upper triangle (row-major, bi <= bj) of a T x T tile grid
+__device__ __forceinline__ void tile_of(int64_t t, int T, int &bi, int &bj) {
+    double TT = (double)T;
+    double disc = (2 * TT + 1) * (2 * TT + 1) - 8.0 * (double)t;
+    int64_t r = (int64_t)floor(((2 * TT + 1) - sqrt(fmax(disc, 0.0))) / 2);
+    auto start = [&](int64_t q) { return q * (2 * (int64_t)T - q + 1) / 2; };
+    if (r < 0) r = 0;
+    if (r > T - 1) r = T - 1;
+    while (r > 0 && start(r) > t) --r;
+    while (r < T - 1 && start(r + 1) <= t) ++r;
+    bi = (int)r;
+    bj = (int)(t - start(r) + r);
+}
+
+struct ScreenArgs {
+    int n;              // nodes
+    int T;              // tiles per side
+    int64_t ntiles;     // T (T + 1) / 2
+    int nk;             // K / BK
+    float lambda;
+    float rel_err;      // margin per unit of the per-node norms
+    int product_margin; // margin rel_err * l_i * l_j (Gaussian) instead of rel_err * (l_i + l_j)
+    const float *l1;    // per-node norms of the margin
+    WTable W;           // pairs with a stored coupling are left to the caller
+    int32_t *out;       // survivors (i, j), i < j
+    int64_t cap;
+    unsigned long long *count;
+    unsigned long long *err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
+                                                       const __grid_constant__ CUtensorMap tB, ScreenArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem, *sB = smem + STAGES * A_BYTES;
+    uint64_t *full = (uint64_t *)(sB + STAGES * B_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;   // [2]
+    uint64_t *acc_empty = acc_full + 2;    // [2]
+    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
+    int *abort = (int *)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full + b, 1);
+            mbar_init(acc_empty + b, 4);  // one arrival per epilogue warp
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {  // TMA producer
+            int64_t kb_all = 0;
+            for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x) {
+                int bi, bj;
+                tile_of(t, a.T, bi, bj);
+                for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
+                    const int s = (int)(kb_all % STAGES);
+                    if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
+                    mbar_expect_tx(full + s, A_BYTES + B_BYTES);
+                    tma_2d(sA + s * A_BYTES, &tA, kb * BK, bi * BM, full + s);
+                    tma_2d(sB + s * B_BYTES, &tB, kb * BK, bj * BN, full + s);
+                }
+            }
+            // let every copy issued above land before the CTA can leave
+            if (kb_all > 0) {
+                const int64_t first = kb_all > STAGES ? kb_all - STAGES : 0;
+                for (int64_t q = first; q < kb_all; ++q) {
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try(full + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
+                        if (gtimer() - t0 > 1000000000ull) break;
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {  // MMA issuer
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            int64_t kb_all = 0, it = 0;
+            for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x, ++it) {
+                const int b = (int)(it & 1);
+                if (!mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
+                    const int s = (int)(kb_all % STAGES);
+                    if (!mbar_wait(full + s, (uint32_t)((kb_all / STAGES) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                    mma_commit(empty + s);
+                }
+                mma_commit(acc_full + b);
+                if (!ok) break;
+            }
+        }
+    } else {  // epilogue warps 0-3: row 32*warp + lane of each tile
+        int64_t it = 0;
+        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+            const int b = (int)(it & 1);
+            if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
+            tc_fence_after();
+            int bi, bj;
+            tile_of(t, a.T, bi, bj);
+            const int i = bi * BM + 32 * warp + lane;
+            const float li = i < a.n ? a.l1[i] : 0.f;
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t r[32];
+                TMEM_LD32(r, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN + 32 * c));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int j0 = bj * BN + 32 * c;
+                const float lj_lane = (j0 + lane) < a.n ? a.l1[j0 + lane] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + q;
+                    const float lj = __shfl_sync(0xffffffffu, lj_lane, q);
+                    const float g = __uint_as_float(r[q]);
+                    const float margin = a.rel_err * (a.product_margin ? li * lj : li + lj);
+                    bool keep = i < j && j < a.n && fabsf(g) > a.lambda - margin;
+                    if (keep) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                    if (bal) {
+                        unsigned long long base = 0;
+                        if (lane == 0) base = atomicAdd(a.count, (unsigned long long)__popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (keep) {
+                            const int64_t pos = (int64_t)base + __popc(bal & ((1u << lane) - 1u));
+                            if (pos < a.cap) {
+                                a.out[2 * pos] = i;
+                                a.out[2 * pos + 1] = j;
+                            }
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty + b);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+    if (threadIdx.x == 0 && *abort) atomicOr(a.err + CNT_ERR, (unsigned long long)ERR_TIMEOUT);
+}
+
+// Ising operands: A_i = [r_i | x_i], B_i = [x_i | r_i] (bf16), r = x - t, and
+// l1_i = sum_m |r_i|; padding samples have r = 0
+__global__ void k_prep_ising(IsingView v, __nv_bfloat16 *A, __nv_bfloat16 *B, float *l1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const int K = 2 * v.Mp;
+    float s = 0.f;
+    for (int m = lane; m < v.Mp; m += 32) {
+        const float x = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? -1.f : 1.f;
+        const float r = m < v.M ? x - v.t[i * v.Mp + m] : 0.f;
+        const __nv_bfloat16 rb = __float2bfloat16_rn(r), xb = __float2bfloat16_rn(x);
+        A[i * K + m] = rb;
+        A[i * K + v.Mp + m] = xb;
+        B[i * K + m] = xb;
+        B[i * K + v.Mp + m] = rb;
+        s += fabsf(r);
+    }
+    s = warp_sum(s);
+    if (lane == 0) l1[i] = s;
+}
+
+// Gaussian operands: A_i = [e_i | x_i], B_i = [x_i | e_i] (bf16), and the
+// margin's per-node norm l_i = |e_i|_2 + |x_i|_2
+__global__ void k_prep_gauss(GaussView v, __nv_bfloat16 *A, __nv_bfloat16 *B, float *l1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const int K = 2 * v.Mp;
+    float se = 0.f, sx = 0.f;
+    for (int m = lane; m < v.Mp; m += 32) {
+        const float x = v.xg[i * v.Mp + m], e = m < v.M ? v.e[i * v.Mp + m] : 0.f;
+        const __nv_bfloat16 eb = __float2bfloat16_rn(e), xb = __float2bfloat16_rn(x);
+        A[i * K + m] = eb;
+        A[i * K + v.Mp + m] = xb;
+        B[i * K + m] = xb;
+        B[i * K + v.Mp + m] = eb;
+        se += e * e;
+        sx += x * x;
+    }
+    se = warp_sum(se);
+    sx = warp_sum(sx);
+    if (lane == 0) l1[i] = sqrtf(se) + sqrtf(sx);  // |e|_2 + |x|_2, combined with the partner's by the margin
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+}  // namespace
+
+// bf16 operand rows of K = 2 Mp entries; survivors of the screen into out
+cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1) {
+    const int64_t warps = c->N;
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    if (c->model == RECON_ISING)
+        k_prep_ising<<<grid, 256, 0, c->stream>>>(c->iv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, l1);
+    else
+        k_prep_gauss<<<grid, 256, 0, c->stream>>>(c->gv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, l1);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Margin per unit of the operands' norms: bf16 rounding (unit roundoff 2^-8)
+// of one operand (Ising: spins are exact) or both (Gaussian), plus a generous
+// allowance for the f32 accumulation inside the tensor core.
+// Ising: |dg_ij| <= u (|r_i|_1 + |r_j|_1) with u = 2^-8 (the spins are exact),
+//   plus the accumulation error, at most K 2^-23 times the same sum.
+// Gaussian: both operands are rounded, |dg_ij| <= (2u + u^2) sum_m (|e_i x_j| + |x_i e_j|)
+//   <= (2u + u^2)(|e_i|_2 |x_j|_2 + |x_i|_2 |e_j|_2) <= (2u + u^2) l_i l_j with
+//   l = |e|_2 + |x|_2 (Cauchy-Schwarz), plus the accumulation error.
+float screen_rel_err(int model, int Mp) {
+    const double u = 1.0 / 256.0, acc = 2.0 * Mp * 1.2e-7;
+    if (model == RECON_ISING) return (float)(u + acc);
+    return (float)(2 * u + u * u + acc);
+}
+
+cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
+                          unsigned long long *count, float margin_scale, int *tiles_out) {
+    if (!g_encode) {
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&g_encode, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || !g_encode) return e != cudaSuccess ? e : cudaErrorNotSupported;
+    }
+    const int K = 2 * (int)c->Mp;
+    CUtensorMap ta, tb;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
+    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t es[2] = {1, 1};
+    if (g_encode(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(A), dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        g_encode(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256;
+    cudaError_t e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ScreenArgs a;
+    a.n = (int)c->N;
+    a.T = (int)((c->N + BM - 1) / BM);
+    a.ntiles = (int64_t)a.T * (a.T + 1) / 2;
+    a.nk = K / BK;
+    a.lambda = (float)c->opt.lambda;
+    a.rel_err = margin_scale;
+    a.product_margin = c->model == RECON_GAUSSIAN;
+    a.l1 = l1;
+    a.W = c->W;
+    a.out = out;
+    a.cap = cap;
+    a.count = count;
+    a.err = c->cnt;
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);
+    k_screen<<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    note_launch();
+    if (tiles_out) *tiles_out = (int)std::min<int64_t>(a.ntiles, 0x7fffffff);
+    return cudaGetLastError();
+}

@@ -1010,6 +1010,12 @@ static recon_status finish_results(recon_ctx *c, int64_t m, int64_t *count) {
 }
 
 recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count) {
+    if (c->opt.knn_mode == RECON_KNN_SCREEN) {
+        c->stats.levels = 0;
+        c->stats.knn_iters = 0;
+        c->stats.level_size[0] = c->N;
+        return screen_run(c, m, pairs_dev, d_dev, count);
+    }
     SearchBufs &S = SB(c);
     S.res_n = 0;
     c->stats.levels = 0;
@@ -1111,6 +1117,86 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
             break;
         }
     }
+    recon_status st = finish_results(c, m, count);
+    if (st != RECON_OK) return st;
+    *pairs_dev = (int32_t *)S.out_pairs.p;
+    *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}
+
+// The exact m best pairs through the tensor-core screen: every pair that can
+// have a nonzero gain survives the screen (see screen.cu); those and the stored
+// couplings are scored exactly, and the m best of them are returned.
+recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count) {
+    SearchBufs &S = SB(c);
+    S.res_n = 0;
+    const int64_t N = c->N, K = 2 * c->Mp;
+    GROW(S.scr_A, sizeof(uint16_t) * (size_t)N * K);
+    GROW(S.scr_B, sizeof(uint16_t) * (size_t)N * K);
+    GROW(S.scr_l1, sizeof(float) * N);
+    CKS(launch_screen_prep(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p));
+    int64_t nnz = 0;
+    {
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
+        CKS(launch_table_count(c->W, counter(c, CNT_SCRATCH0), c->stream));
+        unsigned long long v = 0;
+        recon_status st = read_counter(c, CNT_SCRATCH0, &v);
+        if (st != RECON_OK) return st;
+        nnz = (int64_t)v;
+    }
+    int64_t cap = std::max<int64_t>(int64_t(1) << 20, 16 * m);
+    const float rel = screen_rel_err(c->model, (int)c->Mp);
+    unsigned long long nsurv = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        GROW(S.cand, sizeof(int32_t) * 2 * (cap + nnz + 1));
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH1), 0, sizeof(unsigned long long), c->stream));
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (c->opt.timing) {
+            for (cudaEvent_t *ev : {&ea, &eb}) {
+                if (!c->event_pool.empty()) {
+                    *ev = c->event_pool.back();
+                    c->event_pool.pop_back();
+                } else
+                    CKS(cudaEventCreate(ev));
+            }
+            CKS(cudaEventRecord(ea, c->stream));
+        }
+        int tiles = 0;
+        CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
+                          counter(c, CNT_SCRATCH1), rel, &tiles));
+        if (c->opt.timing) {
+            CKS(cudaEventRecord(eb, c->stream));
+            c->timed.push_back({ea, eb, -1});
+            c->stats.screen_flop += 2.0 * 128.0 * 128.0 * (double)K * (double)tiles;
+        }
+        recon_status st = read_counter(c, CNT_SCRATCH1, &nsurv);
+        if (st != RECON_OK) return st;
+        st = check_err_flags(c, "screen");
+        if (st != RECON_OK) {
+            c->broken = true;
+            return set_err(c, RECON_ETIMEOUT, "the tensor-core screen gave up waiting");
+        }
+        if ((int64_t)nsurv <= cap) break;
+        cap = (int64_t)nsurv + nsurv / 4 + 1024;
+    }
+    if ((int64_t)nsurv > cap) return set_err(c, RECON_ENOMEM, "screen survivors exceed the buffer");
+    c->stats.screen_survivors += (int64_t)nsurv;
+    // the stored couplings, appended after the survivors
+    if (nnz > 0) {
+        GROW(S.ex_d, sizeof(float) * (nnz + 1));
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH2), 0, sizeof(unsigned long long), c->stream));
+        CKS(launch_table_dump(c->W, (int32_t *)S.cand.p + 2 * nsurv, (float *)S.ex_d.p, counter(c, CNT_SCRATCH2),
+                              c->stream));
+    }
+    const int64_t P = (int64_t)nsurv + nnz;
+    GROW(S.res_pairs, sizeof(int32_t) * 2 * std::max<int64_t>(P, 1));
+    GROW(S.res_d, sizeof(float) * std::max<int64_t>(P, 1));
+    if (P > 0) {
+        recon_status st = score_pairs_device(c, (int32_t *)S.cand.p, P, nullptr, (float *)S.res_d.p, nullptr);
+        if (st != RECON_OK) return st;
+        CKS(cudaMemcpyAsync(S.res_pairs.p, S.cand.p, sizeof(int32_t) * 2 * P, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    S.res_n = P;
     recon_status st = finish_results(c, m, count);
     if (st != RECON_OK) return st;
     *pairs_dev = (int32_t *)S.out_pairs.p;

@@ -23,6 +23,7 @@ struct SearchBufs {
     DBuf fk, fv, fk2, fv2;                        // final ordering
     DBuf out_pairs, out_d;                        // result
     DBuf sort_k2, sort_v2, sort_tmp;              // radix sort scratch
+    DBuf scr_A, scr_B, scr_l1;                    // screen operands
     int64_t res_n = 0;
 
     std::vector<DBuf *> all() {
@@ -30,7 +31,7 @@ struct SearchBufs {
                 &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &seg_node, &seg_start, &seg_count, &seg_vbase, &off_t, &off_v, &off_d, &off_sv,
                 &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
                 &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
-                &out_d, &sort_k2, &sort_v2, &sort_tmp};
+                &out_d, &sort_k2, &sort_v2, &sort_tmp, &scr_A, &scr_B, &scr_l1};
     }
 };
 
@@ -38,4 +39,5 @@ void free_search_bufs(SearchBufs *sb);
 recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, const int32_t *gid, float *d,
                                 float *w);
 recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
+recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
 recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librecon.so")
 RECON_OK, RECON_EINVAL, RECON_ENOMEM, RECON_ECUDA, RECON_ETIMEOUT, RECON_ESTATE, RECON_EUNSUPPORTED = range(7)
 RECON_ISING, RECON_GAUSSIAN = 0, 1
 RECON_X_INT8, RECON_X_FP32 = 0, 1
-RECON_KNN_NNDESCENT, RECON_KNN_EXHAUSTIVE, RECON_KNN_AUTO = 0, 1, 2
+RECON_KNN_NNDESCENT, RECON_KNN_EXHAUSTIVE, RECON_KNN_AUTO, RECON_KNN_SCREEN = 0, 1, 2, 3
 RECON_SEED_RANDOM, RECON_SEED_SCREEN, RECON_SEED_LEARNED = 0, 1, 2
 STATUS_NAMES = ["RECON_OK", "RECON_EINVAL", "RECON_ENOMEM", "RECON_ECUDA", "RECON_ETIMEOUT", "RECON_ESTATE",
                 "RECON_EUNSUPPORTED"]
@@ -35,7 +35,9 @@ class recon_stats(C.Structure):
     _fields_ = [("pair_evals", C.c_int64), ("newton_passes", C.c_int64), ("knn_iters", C.c_int64),
                 ("levels", C.c_int32), ("level_k", C.c_int32 * 16), ("level_size", C.c_int64 * 17),
                 ("nnz", C.c_int64), ("samples", C.c_int64), ("kernel_launches", C.c_int64),
-                ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double)]
+                ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double),
+                ("screen_launches", C.c_int64), ("screen_ms", C.c_double), ("screen_flop", C.c_double),
+                ("screen_survivors", C.c_int64)]
 
 
 class ReconError(RuntimeError):
@@ -241,7 +243,8 @@ def recon_get_stats(ctx) -> dict:
             "levels": s.levels, "level_k": list(s.level_k[:max(s.levels, 0)]),
             "level_size": list(s.level_size[:max(s.levels, 0) + 1]), "nnz": s.nnz, "samples": s.samples,
             "kernel_launches": s.kernel_launches, "score_launches": s.score_launches,
-            "score_pairs": s.score_pairs, "score_ms": s.score_ms}
+            "score_pairs": s.score_pairs, "score_ms": s.score_ms, "screen_launches": s.screen_launches,
+            "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors}
 
 
 def recon_save(ctx, path: str):

@@ -1,0 +1,113 @@
+"""The tensor-core gradient screen (RECON_KNN_SCREEN): its best pairs must be
+the exact best pairs — the screen only discards pairs whose gain is provably
+zero, and the survivors are scored exactly.  Checked against the oracle and
+against the CUDA-core exhaustive search, element by element, on sizes with
+ragged tiles (N not a multiple of 128, M not a multiple of 64)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2401_01404_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL, FLOOR = 1e-5, 1e-5
+
+
+@pytest.fixture(scope="module")
+def R():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon
+
+    return recon
+
+
+def _wl(N, M, seed):
+    edges = inputs.erdos_renyi(N, 3, inputs.rng(seed, inputs.GRAPH))
+    w = inputs.rng(seed, inputs.COUPLINGS).normal(0, 0.5, len(edges))
+    h = inputs.rng(seed, inputs.FIELDS).normal(0, 0.1, N)
+    return inputs.gibbs_ising(N, edges, w, h, M, 150, seed)
+
+
+def _close(g_gpu, g_ref):
+    tol = REL * np.abs(g_ref) + FLOOR * max(float(np.max(g_ref)), 1e-30)
+    return np.abs(np.asarray(g_gpu, dtype=np.float64) - g_ref) <= tol
+
+
+@pytest.mark.parametrize("N,M,c", [(100, 200, 1.0), (300, 130, 0.5), (257, 1000, 1.0), (129, 37, 0.7)])
+def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c):
+    X = _wl(N, M, 100 + N)
+    lam = inputs.default_lambda(N, M, c)
+    o = oracle.IsingOracle(X, lam)
+    allp = oracle.all_pairs(np.arange(N))
+    g_ref, _ = o.score(allp)
+    npos = int((g_ref > 1e-6 * g_ref.max()).sum())
+    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    kappa = (len(allp) + 0.4) / N  # ask for every pair: the screen returns exactly its survivors
+    p, d = scr.best_pairs(4, kappa)
+    found = {tuple(x) for x in p.tolist()}
+    pos = {tuple(x) for x, g in zip(allp.tolist(), g_ref) if g > 1e-6 * g_ref.max()}
+    assert pos <= found, len(pos - found)
+    st = scr.stats()
+    assert st["screen_launches"] == 1 and st["screen_survivors"] == len(p)
+    assert len(p) < len(allp) or npos > len(allp) // 2  # the screen discarded pairs
+    gd = dict(zip(map(tuple, allp.tolist()), g_ref))
+    assert _close(-d, np.array([gd[x] for x in map(tuple, p.tolist())])).all()
+
+
+@pytest.mark.parametrize("N,M,kappa", [(200, 300, 1.0), (500, 500, 2.0), (1100, 250, 1.0)])
+def test_screen_best_equals_exhaustive(R, N, M, kappa):
+    X = _wl(N, M, 200 + N)
+    lam = inputs.default_lambda(N, M)
+    Xs = np.ascontiguousarray(X.T)
+    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    ex = R.Recon(Xs, R.RECON_ISING, lam=lam)
+    m = int(math.floor(kappa * N + 0.5))
+    p1, d1 = scr.best_pairs(8, kappa)
+    p2, d2 = ex.exhaustive_best(m)
+    pos2 = d2 < -1e-6 * max(-d2.min(), 1e-30)
+    # every positive-gain pair of the exact answer, except float ties at the cut
+    cut = d2[pos2].max() if pos2.any() else 0.0
+    strict = {tuple(x) for x, dv in zip(p2.tolist(), d2) if dv < cut - 1e-4 * abs(cut)}
+    assert strict <= {tuple(x) for x in p1.tolist()}
+    n = min(len(d1), len(d2))
+    assert np.allclose(d1[:n], d2[:n], rtol=1e-5, atol=1e-5 * abs(d2.min()))
+
+
+def test_screen_with_couplings_and_in_gcd(R, oracle):
+    """After GCD steps W is nonzero: stored couplings are rescored too, and a
+    screen-driven GCD reaches the oracle's optimum."""
+    N, M = 60, 300
+    X = _wl(N, M, 301)
+    lam = inputs.default_lambda(N, M, 0.5)
+    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    for _ in range(400):
+        delta, obj, m = scr.gcd_step(4, 1.0)
+        if delta < 1e-6:
+            break
+    o = oracle.IsingOracle(X, lam)
+    oracle.gcd(o, kappa=1.0, eps=1e-9, max_iters=3000)
+    assert scr.objective() == pytest.approx(o.objective(), rel=1e-6)
+
+
+def test_screen_gaussian(R, oracle):
+    L1, L2, M = 9, 13, 300
+    X = inputs.gaussian_torus_samples(L1, L2, -0.2, 1.8, M, 4000).astype(np.float32).astype(np.float64)
+    N = L1 * L2
+    lam = 0.05 * math.sqrt(M)
+    o = oracle.GaussOracle(X, lam)
+    allp = oracle.all_pairs(np.arange(N))
+    g_ref, _ = o.score(allp)
+    scr = R.Recon(np.ascontiguousarray(X.T.astype(np.float32)), R.RECON_GAUSSIAN, lam=lam,
+                  knn_mode=R.RECON_KNN_SCREEN)
+    p, d = scr.best_pairs(4, (len(allp) + 0.4) / N)
+    found = {tuple(x) for x in p.tolist()}
+    pos = {tuple(x) for x, g in zip(allp.tolist(), g_ref) if g > 1e-6 * g_ref.max()}
+    assert pos <= found
