@@ -235,33 +235,40 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             tile_of(t, a.T, bi, bj);
             const int i = bi * BM + 32 * warp + lane;
             const float li = i < a.n ? a.l1[i] : 0.f;
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t r[32];
-                TMEM_LD32(r, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN + 32 * c));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int j0 = bj * BN + 32 * c;
-                const float lj_lane = (j0 + lane) < a.n ? a.l1[j0 + lane] : 0.f;
+            // two passes over the accumulator: count this warp's survivors, reserve
+            // their slots with one atomic, then write them
+            unsigned long long base = 0, taken = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t r[32];
+                    TMEM_LD32(r, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN + 32 * c));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int j0 = bj * BN + 32 * c;
+                    const float lj_lane = (j0 + lane) < a.n ? a.l1[j0 + lane] : 0.f;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int j = j0 + q;
-                    const float lj = __shfl_sync(0xffffffffu, lj_lane, q);
-                    const float g = __uint_as_float(r[q]);
-                    const float margin = a.rel_err * (a.product_margin ? li * lj : li + lj);
-                    bool keep = i < j && j < a.n && fabsf(g) > a.lambda - margin;
-                    if (keep) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
-                    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                    if (bal) {
-                        unsigned long long base = 0;
-                        if (lane == 0) base = atomicAdd(a.count, (unsigned long long)__popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (keep) {
-                            const int64_t pos = (int64_t)base + __popc(bal & ((1u << lane) - 1u));
+                    for (int q = 0; q < 32; ++q) {
+                        const int j = j0 + q;
+                        const float lj = __shfl_sync(0xffffffffu, lj_lane, q);
+                        const float g = __uint_as_float(r[q]);
+                        const float margin = a.rel_err * (a.product_margin ? li * lj : li + lj);
+                        bool keep = i < j && j < a.n && fabsf(g) > a.lambda - margin;
+                        if (keep) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
+                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                        if (pass == 1 && keep) {
+                            const int64_t pos = (int64_t)(base + taken) + __popc(bal & ((1u << lane) - 1u));
                             if (pos < a.cap) {
                                 a.out[2 * pos] = i;
                                 a.out[2 * pos + 1] = j;
                             }
                         }
+                        taken += (unsigned long long)__popc(bal);
                     }
+                }
+                if (pass == 0) {
+                    if (taken == 0) break;
+                    if (lane == 0) base = atomicAdd(a.count, taken);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    taken = 0;
                 }
             }
             tc_fence_before();
@@ -375,8 +382,12 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256;
-    cudaError_t e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static int attr_device = -1;  // the attribute is per device; set it once for each
+    if (attr_device != c->device) {
+        cudaError_t e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_device = c->device;
+    }
     ScreenArgs a;
     a.n = (int)c->N;
     a.T = (int)((c->N + BM - 1) / BM);
