@@ -106,6 +106,7 @@ typedef struct {
     double screen_ms;         /* their summed device time */
     double screen_flop;       /* their algorithmic work: 2 x (128 x 128 tiles) x K per launch */
     int64_t screen_survivors; /* pairs the screen passed on, summed */
+    int64_t seeded_nodes;     /* nodes whose first list held learned seeds (last call) */
 } recon_stats;
 
 /* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,
@@ -213,6 +214,55 @@ recon_status recon_field_sweep(recon_ctx *ctx, double *delta_out);
  * three may be NULL. Synchronous. */
 recon_status recon_gcd_step(recon_ctx *ctx, int32_t k, double kappa, double *delta_out,
                             double *objective_out, int64_t *m_out);
+
+/* ---- learned proposal (Ising) --------------------------------------------
+ * The paper starts NNDescent from random k-out lists (Algorithm 4) and relies
+ * on that randomness to reach every pair eventually (Sec. III).  The learned
+ * proposal only changes where the first FindBest level's lists start: each
+ * node's sketch s_i = Omega^T x_i / sqrt(M) (Omega: 64 random +-1 columns) goes
+ * through an MLP 64 -> 128 (ReLU) -> 32 into an embedding e_i, and the pairs
+ * with the largest |<e_i, e_j>| seed the lists; every seed is scored exactly
+ * before it can stay.  Random seeding is the default and the fallback (an
+ * untrained context seeds at random even with RECON_SEED_LEARNED). */
+
+typedef struct {
+    int32_t steps;          /* full-batch Adam steps (Kingma and Ba, 2015) */
+    float lr;               /* learning rate */
+    uint64_t seed;          /* initial weights (on the first use) and the sketch */
+    int64_t n_pairs;        /* > 0: train on these host pairs ... */
+    const int32_t *pairs;   /* ... n_pairs x 2 */
+    const float *targets;   /* their targets; NULL: tau = sign(w*) sqrt(2 gain) from
+                               the exact scorer, so that tau^2 / 2 is the gain */
+    int64_t n_best;         /* n_pairs == 0: train on the n_best exact best pairs (tensor-core
+                               screen, default N) ... */
+    int64_t n_random;       /* ... and n_random uniform random pairs (default 8N) */
+    int32_t reserved[8];
+} recon_train_opts;
+
+/* Parameters: W1 [128 x 64] | b1 [128] | W2 [32 x 128] | b2 [32], row-major, FP32
+ * (the forward pass uses their BF16 rounding with FP32 accumulation). */
+int64_t recon_proposal_param_count(void);
+void recon_default_train_opts(recon_train_opts *opts);
+
+/* recon_proposal_train -- trains the proposal on exact pair scores of this
+ * context's data (loss mean (<e_i,e_j> - tau_ij)^2).  loss_out: steps floats
+ * (host), the loss before each step, may be NULL.  Synchronous. */
+recon_status recon_proposal_train(recon_ctx *ctx, const recon_train_opts *opts, float *loss_out);
+
+/* recon_proposal_weights -- copies the parameters out (get_out) and/or in
+ * (set_in, which also restarts Adam and makes the proposal usable for seeding);
+ * host arrays of recon_proposal_param_count() floats.  Weights trained on one
+ * context can be set into another (for example a smaller run's). Synchronous. */
+recon_status recon_proposal_weights(recon_ctx *ctx, float *get_out, const float *set_in, int64_t count);
+
+/* recon_proposal_embed -- sketches (N x 64) and embeddings (N x 32) of every
+ * node under the current weights; host arrays, either may be NULL. */
+recon_status recon_proposal_embed(recon_ctx *ctx, float *sketch_out, float *embed_out);
+
+/* recon_proposal_grad -- loss and its gradient (recon_proposal_param_count()
+ * floats, host) for the given host pairs and targets, without a step. */
+recon_status recon_proposal_grad(recon_ctx *ctx, const int32_t *pairs, const float *targets, int64_t P,
+                                 float *grad_out, double *loss_out);
 
 /* recon_get_model -- the current couplings and per-node parameters.
  *   ij: cap x 2 int32, w: cap floats; receive the stored couplings (i < j),

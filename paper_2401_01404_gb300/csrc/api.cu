@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "proposal.cuh"
 #include "search.cuh"
 
 static thread_local std::string g_err;  // errors without a context
@@ -157,6 +158,7 @@ static void free_ctx(recon_ctx *c) {
     for (DBuf &b : c->bufs)
         if (b.p) cudaFree(b.p);
     free_search_bufs(c->sb);
+    free_proposal(c->prop);
     delete c;
 }
 
@@ -248,7 +250,10 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     if (model == RECON_ISING && o.w_clamp > 8.f)
         return set_err(nullptr, RECON_EINVAL, "w_clamp above 8 is not supported for the Ising model");
     if (o.knn_mode < 0 || o.knn_mode > 3) return set_err(nullptr, RECON_EINVAL, "unknown knn_mode");
-    if (o.seed_mode != RECON_SEED_RANDOM) return set_err(nullptr, RECON_EUNSUPPORTED, "seed_mode not built");
+    if (o.seed_mode != RECON_SEED_RANDOM && o.seed_mode != RECON_SEED_LEARNED)
+        return set_err(nullptr, RECON_EUNSUPPORTED, "seed_mode: RANDOM or LEARNED (the screen is knn_mode SCREEN)");
+    if (o.seed_mode == RECON_SEED_LEARNED && model != RECON_ISING)
+        return set_err(nullptr, RECON_EUNSUPPORTED, "the learned proposal is built for the Ising model");
     const int64_t Mp = (M + 31) / 32 * 32;
     if (model == RECON_ISING && Mp / 32 > ising_max_words())
         return set_err(nullptr, RECON_EUNSUPPORTED, "the Ising path supports M <= %d", 32 * ising_max_words());

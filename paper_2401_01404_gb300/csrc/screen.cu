@@ -133,6 +133,7 @@ struct ScreenArgs {
     int product_margin; // margin rel_err * l_i * l_j (Gaussian) instead of rel_err * (l_i + l_j)
     const float *l1;    // per-node norms of the margin
     WTable W;           // pairs with a stored coupling are left to the caller
+    int skip_stored;    // leave out pairs that hold a stored coupling
     int32_t *out;       // survivors (i, j), i < j
     int64_t cap;
     unsigned long long *count;
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             int bi, bj;
             tile_of(t, a.T, bi, bj);
             const int i = bi * BM + 32 * warp + lane;
-            const float li = i < a.n ? a.l1[i] : 0.f;
+            const float li = (a.l1 && i < a.n) ? a.l1[i] : 0.f;
             // two passes over the accumulator: count this warp's survivors, reserve
             // their slots with one atomic, then write them
             unsigned long long base = 0, taken = 0;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     TMEM_LD32(r, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN + 32 * c));
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                     const int j0 = bj * BN + 32 * c;
-                    const float lj_lane = (j0 + lane) < a.n ? a.l1[j0 + lane] : 0.f;
+                    const float lj_lane = (a.l1 && (j0 + lane) < a.n) ? a.l1[j0 + lane] : 0.f;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const int j = j0 + q;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                         const float g = __uint_as_float(r[q]);
                         const float margin = a.rel_err * (a.product_margin ? li * lj : li + lj);
                         bool keep = i < j && j < a.n && fabsf(g) > a.lambda - margin;
-                        if (keep) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
+                        if (keep && a.skip_stored) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
                         const unsigned bal = __ballot_sync(0xffffffffu, keep);
                         if (pass == 1 && keep) {
                             const int64_t pos = (int64_t)(base + taken) + __popc(bal & ((1u << lane) - 1u));
@@ -360,15 +361,16 @@ float screen_rel_err(int model, int Mp) {
     return (float)(2 * u + u * u + acc);
 }
 
-cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
-                          unsigned long long *count, float margin_scale, int *tiles_out) {
+cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
+                             float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
+                             unsigned long long *count, int *tiles_out) {
+    if (K % BK) return cudaErrorInvalidValue;
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&g_encode, 12000,
                                                          cudaEnableDefault, &q);
         if (e != cudaSuccess || !g_encode) return e != cudaSuccess ? e : cudaErrorNotSupported;
     }
-    const int K = 2 * (int)c->Mp;
     CUtensorMap ta, tb;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
@@ -393,11 +395,12 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
     a.T = (int)((c->N + BM - 1) / BM);
     a.ntiles = (int64_t)a.T * (a.T + 1) / 2;
     a.nk = K / BK;
-    a.lambda = (float)c->opt.lambda;
-    a.rel_err = margin_scale;
-    a.product_margin = c->model == RECON_GAUSSIAN;
+    a.lambda = thr;
+    a.rel_err = rel;
+    a.product_margin = product_margin;
     a.l1 = l1;
     a.W = c->W;
+    a.skip_stored = skip_stored ? 1 : 0;
     a.out = out;
     a.cap = cap;
     a.count = count;
@@ -407,4 +410,10 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
     note_launch();
     if (tiles_out) *tiles_out = (int)std::min<int64_t>(a.ntiles, 0x7fffffff);
     return cudaGetLastError();
+}
+
+cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
+                          unsigned long long *count, float margin_scale, int *tiles_out) {
+    return launch_screen_ex(c, A, B, 2 * (int)c->Mp, (float)c->opt.lambda, l1, margin_scale,
+                            c->model == RECON_GAUSSIAN, true, out, cap, count, tiles_out);
 }

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "proposal.cuh"
 #include "search.cuh"
 
 namespace {
@@ -837,14 +838,23 @@ static recon_status knn_exhaustive(recon_ctx *c, const int32_t *gid, int n, int 
 }
 
 // NNDescent on the node set gid[0..n) with lists of k; returns iterations
-static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k, uint64_t seed, int *iters_out) {
+static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k, uint64_t seed, int *iters_out,
+                                  bool learned) {
     SearchBufs &S = SB(c);
     const int64_t nk = (int64_t)n * k;
     const int in_cap = k, Ucap = k + in_cap;
     GROW(S.pairs_tmp, sizeof(int32_t) * 2 * nk);
     // 1. random initial lists, scored
-    k_knn_init<<<nblk(n), 256, 0, c->stream>>>(n, k, seed, (int32_t *)S.knn_id.p); note_launch();
-    CKS(cudaGetLastError());
+    if (learned) {
+        // first level: seeds from the learned embedding, random ids for the rest
+        int64_t nseeded = 0;
+        recon_status st0 = learned_seed_lists(c, n, k, seed, (int32_t *)S.knn_id.p, &nseeded);
+        if (st0 != RECON_OK) return st0;
+        c->stats.seeded_nodes = nseeded;
+    } else {
+        k_knn_init<<<nblk(n), 256, 0, c->stream>>>(n, k, seed, (int32_t *)S.knn_id.p); note_launch();
+        CKS(cudaGetLastError());
+    }
     k_list_pairs<<<nblk(nk), 256, 0, c->stream>>>(n, k, (int32_t *)S.knn_id.p, (int32_t *)S.pairs_tmp.p); note_launch();
     CKS(cudaGetLastError());
     recon_status st = score_pairs_device(c, (int32_t *)S.pairs_tmp.p, nk, gid, (float *)S.knn_d.p, nullptr);
@@ -1063,7 +1073,8 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
             st = knn_exhaustive(c, gid, (int)n, k);
         } else {
             int iters = 0;
-            st = knn_nndescent(c, gid, (int)n, k, mix64(call_seed + (uint64_t)level), &iters);
+            const bool learned = level == 0 && c->opt.seed_mode == RECON_SEED_LEARNED && c->prop && c->prop->trained;
+            st = knn_nndescent(c, gid, (int)n, k, mix64(call_seed + (uint64_t)level), &iters, learned);
             c->stats.knn_iters += iters;
         }
         if (st != RECON_OK) return st;

@@ -37,7 +37,13 @@ class recon_stats(C.Structure):
                 ("nnz", C.c_int64), ("samples", C.c_int64), ("kernel_launches", C.c_int64),
                 ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double),
                 ("screen_launches", C.c_int64), ("screen_ms", C.c_double), ("screen_flop", C.c_double),
-                ("screen_survivors", C.c_int64)]
+                ("screen_survivors", C.c_int64), ("seeded_nodes", C.c_int64)]
+
+
+class recon_train_opts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64), ("n_pairs", C.c_int64),
+                ("pairs", C.c_void_p), ("targets", C.c_void_p), ("n_best", C.c_int64), ("n_random", C.c_int64),
+                ("reserved", C.c_int32 * 8)]
 
 
 class ReconError(RuntimeError):
@@ -66,6 +72,12 @@ _EXPORTS = {
     "recon_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "recon_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "recon_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
+    "recon_proposal_param_count": (C.c_int64, []),
+    "recon_default_train_opts": (None, [C.c_void_p]),
+    "recon_proposal_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "recon_proposal_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "recon_proposal_embed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "recon_proposal_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "recon_last_error": (C.c_char_p, [C.c_void_p]),
     "recon_destroy": (None, [C.c_void_p]),
 }
@@ -244,7 +256,57 @@ def recon_get_stats(ctx) -> dict:
             "level_size": list(s.level_size[:max(s.levels, 0) + 1]), "nnz": s.nnz, "samples": s.samples,
             "kernel_launches": s.kernel_launches, "score_launches": s.score_launches,
             "score_pairs": s.score_pairs, "score_ms": s.score_ms, "screen_launches": s.screen_launches,
-            "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors}
+            "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors,
+            "seeded_nodes": s.seeded_nodes}
+
+
+def recon_proposal_param_count() -> int:
+    return lib().recon_proposal_param_count()
+
+
+def recon_proposal_train(ctx, steps: int = 300, lr: float = 3e-3, seed: int = 7, pairs=None, targets=None,
+                         n_best: int = 0, n_random: int = 0):
+    """Trains the learned proposal; returns the loss before each step."""
+    o = recon_train_opts()
+    lib().recon_default_train_opts(C.byref(o))
+    o.steps, o.lr, o.seed, o.n_best, o.n_random = steps, lr, seed, n_best, n_random
+    keep = []
+    if pairs is not None:
+        p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        keep.append(p)
+        o.pairs, o.n_pairs = p.ctypes.data, len(p)
+        if targets is not None:
+            t = np.ascontiguousarray(np.asarray(targets, dtype=np.float32))
+            keep.append(t)
+            o.targets = t.ctypes.data
+    loss = np.empty(max(steps, 1), dtype=np.float32)
+    _check(lib().recon_proposal_train(ctx, C.byref(o), loss.ctypes.data), ctx)
+    return loss[:steps]
+
+
+def recon_proposal_weights(ctx, set_in=None):
+    """Returns the parameters (W1 | b1 | W2 | b2, FP32); sets them first if given."""
+    n = recon_proposal_param_count()
+    out = np.empty(n, dtype=np.float32)
+    si = None if set_in is None else np.ascontiguousarray(np.asarray(set_in, dtype=np.float32))
+    _check(lib().recon_proposal_weights(ctx, out.ctypes.data, None if si is None else si.ctypes.data, n), ctx)
+    return out
+
+
+def recon_proposal_embed(ctx, N: int):
+    sk = np.empty((N, 64), dtype=np.float32)
+    em = np.empty((N, 32), dtype=np.float32)
+    _check(lib().recon_proposal_embed(ctx, sk.ctypes.data, em.ctypes.data), ctx)
+    return sk, em
+
+
+def recon_proposal_grad(ctx, pairs, targets):
+    p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    t = np.ascontiguousarray(np.asarray(targets, dtype=np.float32))
+    g = np.empty(recon_proposal_param_count(), dtype=np.float32)
+    loss = C.c_double()
+    _check(lib().recon_proposal_grad(ctx, p.ctypes.data, t.ctypes.data, len(p), g.ctypes.data, C.byref(loss)), ctx)
+    return g, loss.value
 
 
 def recon_save(ctx, path: str):
