@@ -157,6 +157,21 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
     t_exh = t0.elapsed_time(t1) / 1e3
     ref.close()
     out = {"exhaustive_fp32_s": t_exh, "m": m}
+    # learned proposal: pretrained on another draw of the same planted model (not
+    # timed, reported apart); on this run the sketch, MLP inference and the seed
+    # pass are inside the timed span
+    from paper_2401_01404_gb300 import inputs
+
+    t_pre = time.perf_counter()
+    other = inputs.ising_workload(wl.name + "_pretrain", wl.N, wl.M, "regular" if "n2000" in wl.name else "er",
+                                  4 if "n2000" in wl.name else 5, "pm" if "n2000" in wl.name else "normal", 0.3, 0.0,
+                                  300, 4242, wl.k, wl.kappa, "cuda")
+    tr = R.Recon(other.samples_major(), R.RECON_ISING, stream=stream, lam=lam)
+    losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
+    weights = R.recon_proposal_weights(tr.ctx)
+    tr.close()
+    out["pretrain"] = {"seconds": time.perf_counter() - t_pre, "loss_first": float(losses[0]),
+                       "loss_last": float(losses[-1]), "data": "another Gibbs draw of the same configuration"}
     # chosen: the bf16 tensor-core screen with exact FP32 re-scoring of its survivors
     scr = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
     scr.best_pairs(k, kappa)  # warm
@@ -175,13 +190,20 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
     out["screen"] = {"tflops": st["screen_flop"] / (st["screen_ms"] / 1e3) / 1e12 if st["screen_ms"] else None,
                      "avg_launch_ms": st["screen_ms"] / max(st["screen_launches"], 1),
                      "survivors_per_call": st["screen_survivors"] / max(st["screen_launches"], 1)}
-    for kk in (k, 2 * k):
+    for kk, learned in ((k, False), (2 * k, False), (k, True)):
         curve = []
         t_hit = None
+        mode = R.RECON_SEED_LEARNED if learned else R.RECON_SEED_RANDOM
         for cap in range(1, 13):
-            ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5)
+            ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
+                          seed_mode=mode)
+            if learned:
+                R.recon_proposal_weights(ctx.ctx, weights)
             ctx.best_pairs(kk, kappa)  # warm
-            ctx2 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5)
+            ctx2 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
+                           seed_mode=mode)
+            if learned:
+                R.recon_proposal_weights(ctx2.ctx, weights)
             t0.record(stream)
             p, d = ctx2.best_pairs(kk, kappa)
             t1.record(stream)
@@ -194,7 +216,7 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
             if rec >= 0.99 and t_hit is None:
                 t_hit = dt
                 break
-        tag = "plain_fp32" if kk == k else f"plain_fp32_k{kk}"
+        tag = ("learned_fp32" if learned else "plain_fp32") + ("" if kk == k else f"_k{kk}")
         out[tag + "_s"] = t_hit
         out[tag + "_curve"] = curve
     return out

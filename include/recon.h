@@ -86,7 +86,12 @@ typedef struct {
     int32_t screen_c;     /* per-node candidates kept by the screen / learned seeding */
     int32_t timing;       /* nonzero: time every pair-scoring launch with CUDA events
                              on the context's stream (see recon_stats.score_ms) */
-    int32_t reserved[7];  /* zero */
+    int32_t no_graphs;    /* nonzero: enqueue NNDescent iterations launch by launch instead of
+                             replaying one captured CUDA graph per iteration */
+    float learned_frac;   /* RECON_SEED_LEARNED: share of each initial list taken from the
+                             proposal's best seeds, in (0, 1]; the rest are random ids
+                             (0 selects the default 0.5) */
+    int32_t reserved[5];  /* zero */
 } recon_options;
 
 typedef struct {
@@ -107,6 +112,9 @@ typedef struct {
     double screen_flop;       /* their algorithmic work: 2 x (128 x 128 tiles) x K per launch */
     int64_t screen_survivors; /* pairs the screen passed on, summed */
     int64_t seeded_nodes;     /* nodes whose first list held learned seeds (last call) */
+    int64_t tuned_threads;    /* block width the autotuner picked for the segmented scorer (0: not yet) */
+    int64_t dropped_offers;   /* NNDescent second neighbours past the per-node cap, and offers past
+                                 a full offer buffer, skipped for an iteration */
 } recon_stats;
 
 /* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,
@@ -183,6 +191,25 @@ recon_status recon_best_pairs(recon_ctx *ctx, int32_t k, double kappa, int32_t *
  * it needs zeroed.  Calls that overlap on the GPU (several host threads or
  * streams) race on the array.  Synchronous. */
 recon_status recon_score_noalloc(recon_ctx *ctx, const int32_t *pairs, int64_t P, float *d_out, float *w_out);
+
+/* recon_set_list_lengths -- per-node list lengths for the first FindBest level
+ * (Algorithm 3 uses one k for all nodes; a per-node k_i in [1, 64] lets the
+ * search spend its effort unevenly, and the level then uses max(k_i, ceil(4m/N))
+ * for node i, which keeps the level's guarantees).  n = N lengths (host), or
+ * n = 0 to return to the uniform k of recon_best_pairs.  Takes effect with
+ * RECON_KNN_NNDESCENT (and AUTO, which then searches by NNDescent). */
+recon_status recon_set_list_lengths(recon_ctx *ctx, const int32_t *k, int64_t n);
+
+/* recon_knn_graph -- the k-NN graph that the first level of the last FindBest
+ * search built (Algorithm 3, first level; Algorithm 4's lists at the end of the
+ * search): row i holds the best list of node i, ascending in d(i, j) = -gain
+ * (ties in the search's internal order), k_i entries then padding (id -1,
+ * d +inf).  Host buffers ids and d (either may be NULL) of cap >= N k entries,
+ * row-major [N x k], node ids global.  *k_out = the row stride k (max k_i),
+ * *n_out = N; both 0 when the last search built no lists (the screen, a level
+ * small enough for the exhaustive base case, or no search yet).  ids = d = NULL
+ * queries the sizes.  EINVAL if cap < N k. Synchronous. */
+recon_status recon_knn_graph(recon_ctx *ctx, int32_t *ids, float *d, int64_t cap, int32_t *k_out, int64_t *n_out);
 
 /* recon_exhaustive_best -- the m best pairs over all N(N-1)/2 pairs, exact
  * (Algorithm 3's exhaustive base case applied to the whole node set); the

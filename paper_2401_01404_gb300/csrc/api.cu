@@ -88,6 +88,7 @@ extern "C" void recon_default_options(recon_options *o) {
     o->knn_mode = RECON_KNN_NNDESCENT;
     o->seed_mode = RECON_SEED_RANDOM;
     o->screen_c = 0;
+    o->learned_frac = 0.5f;
 }
 
 static recon_status read_err_flags(recon_ctx *c, unsigned long long *flags) {
@@ -159,6 +160,7 @@ static void free_ctx(recon_ctx *c) {
         if (b.p) cudaFree(b.p);
     free_search_bufs(c->sb);
     free_proposal(c->prop);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;
 }
 
@@ -250,6 +252,8 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     if (model == RECON_ISING && o.w_clamp > 8.f)
         return set_err(nullptr, RECON_EINVAL, "w_clamp above 8 is not supported for the Ising model");
     if (o.knn_mode < 0 || o.knn_mode > 3) return set_err(nullptr, RECON_EINVAL, "unknown knn_mode");
+    if (!(o.learned_frac >= 0.f && o.learned_frac <= 1.f))
+        return set_err(nullptr, RECON_EINVAL, "learned_frac outside [0, 1]");
     if (o.seed_mode != RECON_SEED_RANDOM && o.seed_mode != RECON_SEED_LEARNED)
         return set_err(nullptr, RECON_EUNSUPPORTED, "seed_mode: RANDOM or LEARNED (the screen is knn_mode SCREEN)");
     if (o.seed_mode == RECON_SEED_LEARNED && model != RECON_ISING)
@@ -482,6 +486,26 @@ extern "C" recon_status recon_field_sweep(recon_ctx *c, double *delta_out) {
     CK(cudaStreamSynchronize(c->stream));
     if (delta_out) *delta_out = r;
     return RECON_OK;
+}
+
+extern "C" recon_status recon_set_list_lengths(recon_ctx *c, const int32_t *k, int64_t n) {
+    LIVE(c);
+    if (n == 0) {
+        c->klen_host.clear();
+        return RECON_OK;
+    }
+    if (n != c->N || !k) return set_err(c, RECON_EINVAL, "give N = %lld lengths (or n = 0 to clear)", (long long)c->N);
+    for (int64_t x = 0; x < n; ++x)
+        if (k[x] < 1 || k[x] > 64) return set_err(c, RECON_EINVAL, "list length %d of node %lld outside [1, 64]", k[x], (long long)x);
+    c->klen_host.assign(k, k + n);
+    return RECON_OK;
+}
+
+extern "C" recon_status recon_knn_graph(recon_ctx *c, int32_t *ids, float *d, int64_t cap, int32_t *k_out,
+                                        int64_t *n_out) {
+    LIVE(c);
+    if (cap < 0) return set_err(c, RECON_EINVAL, "cap < 0");
+    return knn_graph_copy(c, ids, d, cap, k_out, n_out);
 }
 
 extern "C" recon_status recon_gcd_step(recon_ctx *c, int32_t k, double kappa, double *delta_out,

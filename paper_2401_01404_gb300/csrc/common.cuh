@@ -204,6 +204,7 @@ struct recon_ctx {
     int64_t N = 0, M = 0, Mp = 0, Mw = 0;
     recon_options opt{};
     cudaStream_t stream = nullptr;
+    cudaStream_t gstream = nullptr;  // private stream of the captured NNDescent iterations
 
     // Ising
     uint32_t *xbits = nullptr;
@@ -212,6 +213,8 @@ struct recon_ctx {
     float *xg = nullptr, *e = nullptr, *mu = nullptr, *s2 = nullptr, *Q = nullptr;
     // host copy of the samples (sample-major), kept for checkpoints
     std::vector<uint8_t> x_host;
+    // per-node list lengths of the first FindBest level (empty: uniform k)
+    std::vector<int32_t> klen_host;
 
     WTable W{};
     uint64_t w_cap = 0;
@@ -225,6 +228,8 @@ struct recon_ctx {
 
     recon_stats stats{};
     uint64_t stats_calls = 0;  // best-pairs calls so far (seeds each call's random choices)
+    int tuned_threads = 0;     // block width of the segmented scorer, picked by the autotuner
+    int64_t graph_launches_per_iter = 0;  // kernels in one captured NNDescent iteration
     std::string err;
     bool broken = false;
 
@@ -278,7 +283,7 @@ cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32
 cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                    const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
                                    int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out,
-                                   unsigned long long *cnt, cudaStream_t s);
+                                   unsigned long long *cnt, int threads, cudaStream_t s);
 cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
                                 unsigned long long *cnt, cudaStream_t s);
@@ -295,6 +300,10 @@ cudaError_t launch_gauss_objective(GaussView v, double *partials, int nblocks, c
 cudaError_t launch_gauss_score(GaussView v, WTable W, ScoreParams p, const int32_t *pairs, int64_t P,
                                const int32_t *gid, float *d_out, float *w_out,
                                unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_gauss_score_seg(GaussView v, WTable W, ScoreParams p, const int32_t *seg_node,
+                                   const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
+                                   int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out, int threads,
+                                   cudaStream_t s);
 cudaError_t launch_gauss_update(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
                                 unsigned long long *cnt, cudaStream_t s);

@@ -142,6 +142,57 @@ __global__ void __launch_bounds__(256) k_gscore(GaussView v, WTable W, ScorePara
     }
 }
 
+// Segmented form (see k_score_seg in ising.cu): one block per segment, row x
+// (x_x and e_x) staged in shared memory, each warp streams the rows of its
+// candidates with float4 loads.  The block width is a launch parameter (the
+// autotuner picks it).
+__global__ void k_gscore_seg(GaussView v, WTable W, ScoreParams p, const int32_t *seg_node, const int64_t *seg_start,
+                             const int32_t *seg_count, const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
+                             const int32_t *gid, float *d_out) {
+    extern __shared__ float sm[];
+    const int64_t sidx = blockIdx.x;
+    if (sidx >= nseg) return;
+    const int count = seg_count[sidx];
+    if (count <= 0) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float *sx = sm, *se = sm + v.Mp;
+    const int x = seg_node[sidx];
+    const int gx = gid ? gid[x] : x;
+    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) {
+        sx[m] = v.xg[(int64_t)gx * v.Mp + m];
+        se[m] = v.e[(int64_t)gx * v.Mp + m];
+    }
+    __syncthreads();
+    const float s2x = v.s2[gx], Qx = v.Q[gx];
+    const int64_t start = seg_start[sidx];
+    const int vbase = seg_vbase ? seg_vbase[sidx] : 0;
+    const float4 *sx4 = (const float4 *)sx, *se4 = (const float4 *)se;
+    for (int q = warp; q < count; q += nw) {
+        const int64_t pos = start + q;
+        const int vl = cand ? cand[2 * pos + 1] : vbase + q;
+        const int gj = gid ? gid[vl] : vl;
+        const float4 *xj = (const float4 *)(v.xg + (int64_t)gj * v.Mp), *ej = (const float4 *)(v.e + (int64_t)gj * v.Mp);
+        float a0 = 0.f, a1 = 0.f;
+        for (int c4 = lane; c4 < v.Mp / 4; c4 += 32) {
+            const float4 b = __ldg(xj + c4), d = __ldg(ej + c4), ex = se4[c4], xx = sx4[c4];
+            a0 = fmaf(ex.x, b.x, a0);
+            a0 = fmaf(ex.y, b.y, a0);
+            a0 = fmaf(ex.z, b.z, a0);
+            a0 = fmaf(ex.w, b.w, a0);
+            a1 = fmaf(d.x, xx.x, a1);
+            a1 = fmaf(d.y, xx.y, a1);
+            a1 = fmaf(d.z, xx.z, a1);
+            a1 = fmaf(d.w, xx.w, a1);
+        }
+        const float a = -warp_sum(a0 + a1);
+        const float b = s2x * v.Q[gj] + v.s2[gj] * Qx;
+        const float W0 = wt_lookup(W, pair_key(gx, gj));
+        float g, w;
+        gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
+        if (lane == 0) d_out[pos] = -g;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_gupdate(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
                                                  const int32_t *order, int64_t begin, int64_t end, double *delta,
                                                  unsigned long long *cnt) {
@@ -234,6 +285,24 @@ cudaError_t launch_gauss_score(GaussView v, WTable W, ScoreParams p, const int32
     if (P <= 0) return cudaSuccess;
     int64_t cap = (int64_t)1 << 20;
     k_gscore<<<grid_for(P < cap ? P : cap), 256, 0, s>>>(v, W, p, pairs, P, gid, d_out, w_out); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_score_seg(GaussView v, WTable W, ScoreParams p, const int32_t *seg_node,
+                                   const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
+                                   int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out, int threads,
+                                   cudaStream_t s) {
+    if (nseg <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float) * 2 * v.Mp;
+    // the limit depends on M, so it is set for every launch that needs more than
+    // the default (a host-side attribute call, also legal during graph capture)
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_gscore_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_gscore_seg<<<(unsigned)nseg, threads, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
+                                                       gid, d_out);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -398,7 +398,7 @@ __global__ void k_objective(IsingView v, double *partials) {
 // seg_start[s] .. + seg_count[s]; the second node of candidate q is
 // cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
 // in shared memory once; each warp streams the rows of its candidates.
-__global__ void __launch_bounds__(256) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+__global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                                    const int64_t *seg_start, const int32_t *seg_count,
                                                    const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
                                                    const int32_t *gid, float *d_out, unsigned long long *cnt) {
@@ -678,10 +678,10 @@ cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32
 cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                    const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
                                    int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out,
-                                   unsigned long long *cnt, cudaStream_t s) {
+                                   unsigned long long *cnt, int threads, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
     size_t smem = sizeof(float) * 2 * v.Mp + sizeof(uint32_t) * v.Mw;
-    k_score_seg<<<(unsigned)nseg, 256, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
+    k_score_seg<<<(unsigned)nseg, threads, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
                                                   gid, d_out, cnt);
     note_launch();
     return cudaGetLastError();

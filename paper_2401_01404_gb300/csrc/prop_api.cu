@@ -79,19 +79,22 @@ __global__ void k_scatter(int64_t n, const int32_t *t, const int32_t *v, const f
     sd[off[x] + pos] = d[q];
 }
 
-// the k best seeds of each node (smallest key, ties by id), then distinct
-// random ids != x for the rest of the list
-__global__ void k_seed_lists(int n, int k, const int64_t *off, const int32_t *sv, const float *sd, uint64_t seed,
-                             int32_t *ids, int *nseeded) {
+// the best seeds of each node (smallest key, ties by id), at most smax[x] =
+// round(frac klen[x]) of them, then distinct random ids != x up to klen[x];
+// -1 in the rest of the capacity K
+__global__ void k_seed_lists(int n, int K, const int32_t *klen, float frac, const int64_t *off, const int32_t *sv,
+                             const float *sd, uint64_t seed, int32_t *ids, int *nseeded) {
     const int lane = threadIdx.x & 31;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (x >= n) return;
-    int32_t *L = ids + (int64_t)x * k;
+    int32_t *L = ids + (int64_t)x * K;
+    const int k = klen[x];
+    const int smax = min(k, max(1, __float2int_rn(frac * (float)k)));
     const int64_t b = off[x], cntx = off[x + 1] - off[x];
     float last_d = -INFINITY;
     int last_v = -1;
     int q = 0;
-    for (; q < k && q < cntx; ++q) {
+    for (; q < smax && q < cntx; ++q) {
         float best = INFINITY;
         int bv = 0x7fffffff;
         for (int64_t r = lane; r < cntx; r += 32) {
@@ -117,9 +120,11 @@ __global__ void k_seed_lists(int n, int k, const int64_t *off, const int32_t *sv
         last_v = bv;
     }
     __syncwarp();
+    for (int r = k + lane; r < K; r += 32) L[r] = -1;
     if (lane == 0) {
         if (q > 0) atomicAdd(nseeded, 1);
         uint64_t ctr = 0;
+        // k <= n - 1, so the fallback scan always completes the list
         while (q < k) {
             const int y = (int)(mix64(seed ^ mix64(((uint64_t)x << 32) ^ ctr++)) % (uint64_t)n);
             bool dup = y == x;
@@ -322,41 +327,40 @@ extern "C" recon_status recon_proposal_train(recon_ctx *c, const recon_train_opt
 
 // Initial lists of the first FindBest level from the learned embedding: the
 // seed pairs are those with |<e_i, e_j>| above a threshold picked so that the
-// tensor-core pass keeps about 2k seeds per node (estimated from 2^18 random
-// pairs); each node takes its k best seeds and random ids for the rest.
-recon_status learned_seed_lists(recon_ctx *c, int n, int k, uint64_t seed, int32_t *ids, int64_t *nseeded_out) {
+// tensor-core pass keeps about 2 f k_i seeds per node (estimated from 2^14
+// random pairs); each node takes at most f k_i of its best seeds and random ids
+// for the rest (f = learned_frac), so that the search keeps exploring.
+recon_status learned_seed_lists(recon_ctx *c, int n, int K, const int32_t *klen, uint64_t seed, int32_t *ids,
+                                int64_t *nseeded_out) {
     Proposal &P = *c->prop;
+    const float f = c->opt.learned_frac > 0.f ? c->opt.learned_frac : 0.5f;
     CK(proposal_forward(c, P, false));
     CK(grow(P.seedA, sizeof(uint16_t) * (size_t)c->N * 64, c->stream));
     CK(proposal_seed_operands(c, P, P.seedA.p));
     // threshold from a sample
-    const int64_t ns = 1 << 18;
-    DBuf sp, sv;
-    CK(grow(sp, sizeof(int32_t) * 2 * ns, c->stream));
-    CK(grow(sv, sizeof(float) * ns, c->stream));
-    k_rand_pairs<<<nbk(ns), 256, 0, c->stream>>>(ns, n, mix64(seed ^ 0x5a3d1eull), (int32_t *)sp.p);
+    const int64_t ns = 1 << 14;
+    CK(grow(P.s_pairs, sizeof(int32_t) * 2 * ns, c->stream));
+    CK(grow(P.s_vals, sizeof(float) * ns, c->stream));
+    k_rand_pairs<<<nbk(ns), 256, 0, c->stream>>>(ns, n, mix64(seed ^ 0x5a3d1eull), (int32_t *)P.s_pairs.p);
     note_launch();
-    k_absdot<<<nbk(ns), 256, 0, c->stream>>>(ns, (int32_t *)sp.p, (float *)P.emb.p, (float *)sv.p);
+    k_absdot<<<nbk(ns), 256, 0, c->stream>>>(ns, (int32_t *)P.s_pairs.p, (float *)P.emb.p, (float *)P.s_vals.p);
     note_launch();
     std::vector<float> hv(ns);
-    CK(cudaMemcpyAsync(hv.data(), sv.p, sizeof(float) * ns, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hv.data(), P.s_vals.p, sizeof(float) * ns, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    cudaFree(sp.p);
-    cudaFree(sv.p);
     const double npairs = (double)n * (n - 1) / 2.0;
-    const double frac = std::min(1.0, (double)n * k / npairs);  // about 2k seeds per node (k per endpoint)
+    const double frac = std::min(1.0, (double)f * n * K / npairs);  // about 2 f k seeds per node
     int64_t rank = std::min<int64_t>(ns - 1, (int64_t)(frac * ns));
     std::nth_element(hv.begin(), hv.begin() + (ns - 1 - rank), hv.end());
     const float thr = frac >= 1.0 ? -1.f : hv[ns - 1 - rank];
     // seed pairs through the tensor-core pass (K = 64: 32 embedding dims and zeros)
-    int64_t cap = std::max<int64_t>(4 * (int64_t)n * k, 1 << 16);
+    int64_t cap = std::max<int64_t>((int64_t)(4.0 * f * n * K) + 1024, 1 << 16);
     unsigned long long cnt = 0;
-    DBuf cands;
     for (int attempt = 0; attempt < 3; ++attempt) {
-        CK(grow(cands, sizeof(int32_t) * 2 * cap, c->stream));
+        CK(grow(P.s_cands, sizeof(int32_t) * 2 * cap, c->stream));
         CK(cudaMemsetAsync(c->cnt + CNT_SCRATCH3, 0, sizeof(unsigned long long), c->stream));
         int tiles = 0;
-        CK(launch_screen_ex(c, P.seedA.p, P.seedA.p, 64, thr, nullptr, 0.f, 0, false, (int32_t *)cands.p, cap,
+        CK(launch_screen_ex(c, P.seedA.p, P.seedA.p, 64, thr, nullptr, 0.f, 0, false, (int32_t *)P.s_cands.p, cap,
                             c->cnt + CNT_SCRATCH3, &tiles));
         CK(cudaMemcpyAsync(c->cnt_host + CNT_SCRATCH3, c->cnt + CNT_SCRATCH3, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
@@ -366,45 +370,40 @@ recon_status learned_seed_lists(recon_ctx *c, int n, int k, uint64_t seed, int32
         cap = (int64_t)cnt + (int64_t)cnt / 4 + 1024;
     }
     const int64_t ne = 2 * (int64_t)std::min<unsigned long long>(cnt, (unsigned long long)cap);
-    DBuf ot, ov, od, cntv, offw, off, cur, svv, sdd, tmp;
-    CK(grow(ot, sizeof(int32_t) * (ne + 1), c->stream));
-    CK(grow(ov, sizeof(int32_t) * (ne + 1), c->stream));
-    CK(grow(od, sizeof(float) * (ne + 1), c->stream));
-    CK(grow(svv, sizeof(int32_t) * (ne + 1), c->stream));
-    CK(grow(sdd, sizeof(float) * (ne + 1), c->stream));
-    CK(grow(cntv, sizeof(int32_t) * (n + 1), c->stream));
-    CK(grow(cur, sizeof(int32_t) * (n + 1), c->stream));
-    CK(grow(offw, sizeof(int64_t) * (n + 1), c->stream));
-    CK(grow(off, sizeof(int64_t) * (n + 1), c->stream));
-    CK(grow(tmp, sizeof(int64_t) * scan_tmp_elems(n + 1), c->stream));
+    for (DBuf *b : {&P.s_ot, &P.s_ov, &P.s_sv}) CK(grow(*b, sizeof(int32_t) * (ne + 1), c->stream));
+    for (DBuf *b : {&P.s_od, &P.s_sd}) CK(grow(*b, sizeof(float) * (ne + 1), c->stream));
+    for (DBuf *b : {&P.s_cnt, &P.s_cur}) CK(grow(*b, sizeof(int32_t) * (n + 1), c->stream));
+    for (DBuf *b : {&P.s_offw, &P.s_off}) CK(grow(*b, sizeof(int64_t) * (n + 1), c->stream));
+    CK(grow(P.s_tmp, sizeof(int64_t) * scan_tmp_elems(n + 1), c->stream));
+    int32_t *ot = (int32_t *)P.s_ot.p, *ov = (int32_t *)P.s_ov.p, *cntv = (int32_t *)P.s_cnt.p;
+    float *od = (float *)P.s_od.p;
+    int64_t *off = (int64_t *)P.s_off.p;
     if (ne) {
-        k_seed_offers<<<nbk(ne / 2), 256, 0, c->stream>>>(ne / 2, (int32_t *)cands.p, (float *)P.emb.p, (int32_t *)ot.p,
-                                                          (int32_t *)ov.p, (float *)od.p);
+        k_seed_offers<<<nbk(ne / 2), 256, 0, c->stream>>>(ne / 2, (int32_t *)P.s_cands.p, (float *)P.emb.p, ot, ov, od);
         note_launch();
     }
-    CK(cudaMemsetAsync(cntv.p, 0, sizeof(int32_t) * (n + 1), c->stream));
-    CK(cudaMemsetAsync(cur.p, 0, sizeof(int32_t) * (n + 1), c->stream));
+    CK(cudaMemsetAsync(cntv, 0, sizeof(int32_t) * (n + 1), c->stream));
+    CK(cudaMemsetAsync(P.s_cur.p, 0, sizeof(int32_t) * (n + 1), c->stream));
     if (ne) {
-        k_count<<<nbk(ne), 256, 0, c->stream>>>(ne, (int32_t *)ot.p, (int32_t *)cntv.p);
+        k_count<<<nbk(ne), 256, 0, c->stream>>>(ne, ot, cntv);
         note_launch();
     }
-    k_widen<<<nbk(n + 1), 256, 0, c->stream>>>((int32_t *)cntv.p, (int64_t *)offw.p, n + 1);
+    k_widen<<<nbk(n + 1), 256, 0, c->stream>>>(cntv, (int64_t *)P.s_offw.p, n + 1);
     note_launch();
-    CK(launch_scan_i64((int64_t *)offw.p, (int64_t *)off.p, n + 1, (int64_t *)tmp.p, c->stream));
+    CK(launch_scan_i64((int64_t *)P.s_offw.p, off, n + 1, (int64_t *)P.s_tmp.p, c->stream));
     if (ne) {
-        k_scatter<<<nbk(ne), 256, 0, c->stream>>>(ne, (int32_t *)ot.p, (int32_t *)ov.p, (float *)od.p, (int64_t *)off.p,
-                                                  (int32_t *)cur.p, (int32_t *)svv.p, (float *)sdd.p);
+        k_scatter<<<nbk(ne), 256, 0, c->stream>>>(ne, ot, ov, od, off, (int32_t *)P.s_cur.p, (int32_t *)P.s_sv.p,
+                                                  (float *)P.s_sd.p);
         note_launch();
     }
     CK(cudaMemsetAsync(c->cnt + CNT_SCRATCH3, 0, sizeof(unsigned long long), c->stream));
-    k_seed_lists<<<nbk((int64_t)n * 32), 256, 0, c->stream>>>(n, k, (int64_t *)off.p, (int32_t *)svv.p,
-                                                               (float *)sdd.p, seed, ids, (int *)(c->cnt + CNT_SCRATCH3));
+    k_seed_lists<<<nbk((int64_t)n * 32), 256, 0, c->stream>>>(n, K, klen, f, off, (int32_t *)P.s_sv.p,
+                                                               (float *)P.s_sd.p, seed, ids,
+                                                               (int *)(c->cnt + CNT_SCRATCH3));
     note_launch();
     int nseeded = 0;
     CK(cudaMemcpyAsync(&nseeded, c->cnt + CNT_SCRATCH3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    for (DBuf *b : {&cands, &ot, &ov, &od, &cntv, &offw, &off, &cur, &svv, &sdd, &tmp})
-        if (b->p) cudaFree(b->p);
     if (nseeded_out) *nseeded_out = nseeded;
     return RECON_OK;
 }

@@ -342,7 +342,9 @@ cudaError_t proposal_seed_operands(recon_ctx *c, Proposal &P, void *A) {
 void free_proposal(Proposal *P) {
     if (!P) return;
     for (DBuf *b : {&P->w, &P->m1, &P->m2, &P->g, &P->w1b, &P->w2b, &P->omega, &P->sketch, &P->emb, &P->act, &P->de,
-                    &P->dA, &P->tpairs, &P->ttau, &P->loss, &P->seedA})
+                    &P->dA, &P->tpairs, &P->ttau, &P->loss, &P->seedA, &P->s_pairs, &P->s_vals, &P->s_cands,
+                    &P->s_ot, &P->s_ov, &P->s_od, &P->s_cnt, &P->s_offw, &P->s_off, &P->s_cur, &P->s_sv, &P->s_sd,
+                    &P->s_tmp})
         if (b->p) cudaFree(b->p);
     delete P;
 }

@@ -14,6 +14,8 @@ struct Proposal {
     DBuf emb, act, de, dA;    // embeddings, first-layer pre-activations, gradients
     DBuf tpairs, ttau, loss;  // training pairs, targets, loss accumulator
     DBuf seedA;               // bf16 embedding operands for seeding
+    // seeding scratch, kept between searches
+    DBuf s_pairs, s_vals, s_cands, s_ot, s_ov, s_od, s_cnt, s_offw, s_off, s_cur, s_sv, s_sd, s_tmp;
     bool ready = false;
     bool trained = false;     // set by recon_proposal_train; learned seeding needs it
     int64_t t = 0;            // Adam step
@@ -28,4 +30,5 @@ cudaError_t proposal_grad(recon_ctx *c, Proposal &P, const int32_t *pairs, const
 cudaError_t proposal_adam(recon_ctx *c, Proposal &P, float lr);
 cudaError_t proposal_seed_operands(recon_ctx *c, Proposal &P, void *A);
 void free_proposal(Proposal *P);
-recon_status learned_seed_lists(recon_ctx *c, int n, int k, uint64_t seed, int32_t *ids, int64_t *nseeded_out);
+recon_status learned_seed_lists(recon_ctx *c, int n, int K, const int32_t *klen, uint64_t seed, int32_t *ids,
+                                int64_t *nseeded_out);

@@ -27,17 +27,20 @@
 
 namespace {
 
-constexpr int NND_MAX_K = 32;
+constexpr int NND_MAX_K = 64;  // list capacity handled by the merge (two entries per lane)
 
 __device__ __forceinline__ bool key_less(float da, uint32_t ra, float db, uint32_t rb) {
     return da < db || (da == db && ra < rb);
 }
 
-// random k-out lists (k distinct ids != x), or every other node when k >= n-1
-__global__ void k_knn_init(int n, int k, uint64_t seed, int32_t *ids) {
+// random lists: klen[x] distinct ids != x (every other node when klen >= n-1),
+// -1 in the unused slots of the capacity K
+__global__ void k_knn_init(int n, int K, const int32_t *klen, uint64_t seed, int32_t *ids) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
-    int32_t *L = ids + (int64_t)x * k;
+    int32_t *L = ids + (int64_t)x * K;
+    const int k = klen[x];
+    for (int r = k; r < K; ++r) L[r] = -1;
     int q = 0;
     if (k >= n - 1) {
         for (int y = 0; y < n && q < k; ++y)
@@ -61,19 +64,30 @@ __global__ void k_knn_init(int n, int k, uint64_t seed, int32_t *ids) {
     }
 }
 
-__global__ void k_list_pairs(int n, int k, const int32_t *ids, int32_t *pairs) {
+__global__ void k_list_pairs(int n, int K, const int32_t *ids, const int32_t *klen, int32_t *pairs, int32_t *seg_node,
+                             int64_t *seg_start, int32_t *seg_count) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)n * k) return;
-    pairs[2 * e] = (int32_t)(e / k);
-    pairs[2 * e + 1] = ids[e];
+    if (e >= (int64_t)n * K) return;
+    const int x = (int)(e / K);
+    pairs[2 * e] = x;
+    pairs[2 * e + 1] = ids[e] >= 0 ? ids[e] : x;
+    if (e % K == 0) {
+        seg_node[x] = x;
+        seg_start[x] = e;
+        seg_count[x] = klen[x];
+    }
 }
 
-// sort each initial list by (d, pair hash); every entry is new
-__global__ void k_sort_lists(int n, int k, const int32_t *gid, int32_t *ids, float *dd, uint8_t *isnew) {
+// sort each initial list by (d, pair hash); every entry is new; unused slots
+// hold id -1 and d = +inf
+__global__ void k_sort_lists(int n, int K, const int32_t *klen, const int32_t *gid, int32_t *ids, float *dd,
+                             uint8_t *isnew) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
-    int32_t *L = ids + (int64_t)x * k;
-    float *D = dd + (int64_t)x * k;
+    int32_t *L = ids + (int64_t)x * K;
+    float *D = dd + (int64_t)x * K;
+    const int k = klen[x];
+    for (int r = k; r < K; ++r) D[r] = INFINITY;
     for (int a = 1; a < k; ++a) {
         int32_t id = L[a];
         float d = D[a];
@@ -89,12 +103,12 @@ __global__ void k_sort_lists(int n, int k, const int32_t *gid, int32_t *ids, flo
         L[b + 1] = id;
         D[b + 1] = d;
     }
-    for (int a = 0; a < k; ++a) isnew[(int64_t)x * k + a] = 1;
+    for (int a = 0; a < K; ++a) isnew[(int64_t)x * K + a] = a < k;
 }
 
 __global__ void k_in_count(int64_t nk, const int32_t *ids, int32_t *indeg) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nk) atomicAdd(&indeg[ids[e]], 1);
+    if (e < nk && ids[e] >= 0) atomicAdd(&indeg[ids[e]], 1);
 }
 
 __global__ void k_i32_to_i64(const int32_t *a, int64_t *b, int64_t n) {
@@ -106,23 +120,27 @@ __global__ void k_in_fill(int64_t nk, const int32_t *ids, const int64_t *inoff, 
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nk) return;
     int y = ids[e];
+    if (y < 0) return;
     int pos = atomicAdd(&cursor[y], 1);
     in_e[inoff[y] + pos] = (int32_t)e;
 }
 
 // U(x) = out(x) u (at most in_cap in-neighbours, smallest random priority)
-__global__ void k_build_U(int n, int k, int in_cap, int Ucap, uint64_t seed, const int32_t *ids,
+__global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Ucap, uint64_t seed0, const int *iter,
+                          const int32_t *ids,
                           const uint8_t *isnew, const int64_t *inoff, const int32_t *indeg, const int32_t *in_e,
                           int32_t *U, uint8_t *Uf, int32_t *Udeg) {
     extern __shared__ int32_t sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (x >= n) return;
+    const uint64_t seed = mix64(seed0 ^ (0x5bd1e995ull * (uint64_t)*iter));
     int32_t *sid = sm + wib * 2 * Ucap;
     int32_t *sfl = sid + Ucap;
+    const int k = klen[x];
     for (int r = lane; r < k; r += 32) {
-        sid[r] = ids[(int64_t)x * k + r];
-        sfl[r] = isnew[(int64_t)x * k + r];
+        sid[r] = ids[(int64_t)x * K + r];
+        sfl[r] = isnew[(int64_t)x * K + r];
     }
     __syncwarp();
     int d = k;
@@ -139,7 +157,7 @@ __global__ void k_build_U(int n, int k, int in_cap, int Ucap, uint64_t seed, con
             int best_e = -1;
             for (int q = lane; q < deg; q += 32) {
                 int e = in_e[b + q];
-                uint64_t pr = mix64(seed ^ ((uint64_t)x << 32) ^ (uint64_t)(e / k));
+                uint64_t pr = mix64(seed ^ ((uint64_t)x << 32) ^ (uint64_t)(e / K));
                 if ((s == 0 || pr > last) && (pr < best || (pr == best && e < best_e))) {
                     best = pr;
                     best_e = e;
@@ -157,7 +175,7 @@ __global__ void k_build_U(int n, int k, int in_cap, int Ucap, uint64_t seed, con
             last = best;
             e_sel = best_e;
         }
-        const int y = e_sel / k;
+        const int y = e_sel / K;
         const int fl = isnew[e_sel];
         int found = -1;
         for (int r = lane; r < k; r += 32)
@@ -193,8 +211,8 @@ __device__ __forceinline__ int sh_insert(int32_t *h, int hmask, int32_t v) {
 }
 
 // candidates of x: v in U(U(x)), v > x, not in x's list, reached by a new edge
-__global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *Uf, const int32_t *Udeg,
-                      const int32_t *ids, int hsize, int lcap, int32_t *cand, int64_t cap,
+__global__ void k_gen(int n, int K, const int32_t *klen, int Ucap, const int32_t *U, const uint8_t *Uf,
+                      const int32_t *Udeg, const int32_t *ids, int hsize, int lcap, int32_t *cand, int64_t cap,
                       unsigned long long *counter, unsigned long long *cnt, int32_t *seg_node, int64_t *seg_start,
                       int32_t *seg_count) {
     extern __shared__ int32_t sm[];
@@ -207,10 +225,10 @@ __global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *U
     for (int s = lane; s < hsize; s += 32) h[s] = -1;
     if (lane == 0) *wcount = 0;
     __syncwarp();
-    for (int r = lane; r < k; r += 32) sh_insert(h, hsize - 1, ids[(int64_t)x * k + r]);
+    for (int r = lane; r < klen[x]; r += 32) sh_insert(h, hsize - 1, ids[(int64_t)x * K + r]);
     __syncwarp();
     const int degx = Udeg[x];
-    bool overflow = false;
+    bool overflow = false, dropped = false;
     for (int a = 0; a < degx; ++a) {
         const int j = U[(int64_t)x * Ucap + a];
         const int fxj = Uf[(int64_t)x * Ucap + a];
@@ -219,13 +237,16 @@ __global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *U
             const int v = U[(int64_t)j * Ucap + b];
             const int fjv = Uf[(int64_t)j * Ucap + b];
             if (v > x && (fxj | fjv)) {
+                // past the per-node cap the remaining second neighbours are
+                // skipped this iteration (the paper's cap on the second-neighbour
+                // loop); they stay reachable in later iterations
                 int r = sh_insert(h, hsize - 1, v);
                 if (r == 1) {
                     int pos = atomicAdd(wcount, 1);
                     if (pos < lcap) list[pos] = v;
-                    else overflow = true;
+                    else dropped = true;
                 } else if (r < 0)
-                    overflow = true;
+                    dropped = true;
             }
         }
     }
@@ -248,24 +269,27 @@ __global__ void k_gen(int n, int k, int Ucap, const int32_t *U, const uint8_t *U
         seg_count[x] = count;
     }
     if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_OVERFLOW);
+    if (__any_sync(0xffffffffu, dropped) && lane == 0) atomicAdd(&cnt[CNT_SCRATCH3], 1ull);
 }
 
 // offer each scored candidate to both endpoints if it beats their worst entry
-__global__ void k_offer(int64_t P, const int32_t *cand, const float *dc, int k, const float *knn_d,
-                        int32_t *ot, int32_t *ov, float *od, unsigned long long *counter, int64_t cap,
-                        unsigned long long *cnt) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= P) return;
+__global__ void k_offer(const unsigned long long *Pdev, int64_t Pcap, const int32_t *cand, const float *dc, int K,
+                        const int32_t *klen, const float *knn_d, int32_t *ot, int32_t *ov, float *od,
+                        unsigned long long *counter, int64_t cap, unsigned long long *dropped) {
+    const int64_t P = min((int64_t)*Pdev, Pcap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
     const int x = cand[2 * q], v = cand[2 * q + 1];
     const float d = dc[q];
-    const bool to_x = d < knn_d[(int64_t)x * k + k - 1];
-    const bool to_v = d < knn_d[(int64_t)v * k + k - 1];
+    const bool to_x = d < knn_d[(int64_t)x * K + klen[x] - 1];
+    const bool to_v = d < knn_d[(int64_t)v * K + klen[v] - 1];
     int nn = (int)to_x + (int)to_v;
-    if (!nn) return;
+    if (!nn) continue;
     unsigned long long pos = atomicAdd(counter, (unsigned long long)nn);
-    if ((int64_t)(pos + nn) > cap) {
-        atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_OVERFLOW);
-        return;
+    if ((int64_t)(pos + nn) > cap) {  // offer buffer full: the offer is dropped this iteration
+        atomicAdd(dropped, 1ull);
+        // slots below cap that this offer reserved stay marked empty
+        for (int64_t s = (int64_t)pos; s < (int64_t)pos + nn && s < cap; ++s) ot[s] = -1;
+        continue;
     }
     if (to_x) {
         ot[pos] = x;
@@ -278,68 +302,106 @@ __global__ void k_offer(int64_t P, const int32_t *cand, const float *dc, int k, 
         ov[pos] = x;
         od[pos] = d;
     }
+    }
 }
 
-__global__ void k_count_targets(int64_t P, const int32_t *ot, int32_t *cntv) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < P) atomicAdd(&cntv[ot[q]], 1);
+__global__ void k_count_targets(const unsigned long long *Pdev, int64_t Pcap, const int32_t *ot, int32_t *cntv) {
+    const int64_t P = min((int64_t)*Pdev, Pcap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x)
+        if (ot[q] >= 0) atomicAdd(&cntv[ot[q]], 1);
 }
 
-__global__ void k_scatter_offers(int64_t P, const int32_t *ot, const int32_t *ov, const float *od,
-                                 const int64_t *off, int32_t *cursor, int32_t *sv, float *sd) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= P) return;
-    const int x = ot[q];
-    const int pos = atomicAdd(&cursor[x], 1);
-    sv[off[x] + pos] = ov[q];
-    sd[off[x] + pos] = od[q];
+__global__ void k_scatter_offers(const unsigned long long *Pdev, int64_t Pcap, const int32_t *ot, const int32_t *ov,
+                                 const float *od, const int64_t *off, int32_t *cursor, int32_t *sv, float *sd) {
+    const int64_t P = min((int64_t)*Pdev, Pcap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+        const int x = ot[q];
+        if (x < 0) continue;
+        const int pos = atomicAdd(&cursor[x], 1);
+        sv[off[x] + pos] = ov[q];
+        sd[off[x] + pos] = od[q];
+    }
 }
 
-// best k of (old list u offers) per node; old entries win ties
-__global__ void k_merge(int n, int k, const int32_t *gid, int32_t *ids, float *dd, uint8_t *isnew,
+// iteration counter of a (possibly graph-replayed) NNDescent loop
+__global__ void k_next_iter(int *it) { *it += 1; }
+
+// best k of (old list u offers) per node; old entries win ties.  A warp holds
+// the list, entry r in lane r (slot A) and entry r + 32 in lane r (slot B), so
+// lists of up to 64 entries; node x keeps klen[x] of them.
+__global__ void k_merge(int n, int K, const int32_t *klen, const int32_t *gid, int32_t *ids, float *dd, uint8_t *isnew,
                         const int64_t *off, const int32_t *sv, const float *sd, unsigned long long *delta) {
     const int lane = threadIdx.x & 31;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (x >= n) return;
-    int id = -1;
-    float d = INFINITY;
-    uint32_t rk = 0xffffffffu;
+    const int k = klen[x];
+    int idA = -1, idB = -1;
+    float dA = INFINITY, dB = INFINITY;
+    uint32_t rA = 0xffffffffu, rB = 0xffffffffu;
     if (lane < k) {
-        id = ids[(int64_t)x * k + lane];
-        d = dd[(int64_t)x * k + lane];
-        rk = 0;
+        idA = ids[(int64_t)x * K + lane];
+        dA = dd[(int64_t)x * K + lane];
+        rA = 0;
+    }
+    if (lane + 32 < k) {
+        idB = ids[(int64_t)x * K + lane + 32];
+        dB = dd[(int64_t)x * K + lane + 32];
+        rB = 0;
     }
     const int gx = gid[x];
+    const int last = k - 1;
     for (int64_t q = off[x]; q < off[x + 1]; ++q) {
         const int v = sv[q];
         const float dv = sd[q];
-        if (__any_sync(0xffffffffu, id == v)) continue;
+        if (__any_sync(0xffffffffu, idA == v || idB == v)) continue;
         const uint32_t rv = 1u + (uint32_t)(mix64(pair_key(gx, gid[v])) >> 33);
-        const float dw = __shfl_sync(0xffffffffu, d, k - 1);
-        const uint32_t rw = __shfl_sync(0xffffffffu, rk, k - 1);
+        const float dw = last < 32 ? __shfl_sync(0xffffffffu, dA, last) : __shfl_sync(0xffffffffu, dB, last - 32);
+        const uint32_t rw = last < 32 ? __shfl_sync(0xffffffffu, rA, last) : __shfl_sync(0xffffffffu, rB, last - 32);
         if (!key_less(dv, rv, dw, rw)) continue;
-        const unsigned lt = __ballot_sync(0xffffffffu, lane < k && key_less(d, rk, dv, rv));
-        const int pos = __popc(lt);
-        const int id_up = __shfl_up_sync(0xffffffffu, id, 1);
-        const float d_up = __shfl_up_sync(0xffffffffu, d, 1);
-        const uint32_t rk_up = __shfl_up_sync(0xffffffffu, rk, 1);
-        if (lane > pos && lane < k) {
-            id = id_up;
-            d = d_up;
-            rk = rk_up;
+        const int pos = __popc(__ballot_sync(0xffffffffu, lane < k && key_less(dA, rA, dv, rv))) +
+                        __popc(__ballot_sync(0xffffffffu, lane + 32 < k && key_less(dB, rB, dv, rv)));
+        // shift entries at positions >= pos one place up; the carry into slot B
+        // lane 0 is slot A lane 31
+        const int idA_up = __shfl_up_sync(0xffffffffu, idA, 1), idB_up = __shfl_up_sync(0xffffffffu, idB, 1);
+        const float dA_up = __shfl_up_sync(0xffffffffu, dA, 1), dB_up = __shfl_up_sync(0xffffffffu, dB, 1);
+        const uint32_t rA_up = __shfl_up_sync(0xffffffffu, rA, 1), rB_up = __shfl_up_sync(0xffffffffu, rB, 1);
+        const int idA31 = __shfl_sync(0xffffffffu, idA, 31);
+        const float dA31 = __shfl_sync(0xffffffffu, dA, 31);
+        const uint32_t rA31 = __shfl_sync(0xffffffffu, rA, 31);
+        const int pB = lane + 32;
+        if (pB < k && pB > pos) {
+            idB = lane == 0 ? idA31 : idB_up;
+            dB = lane == 0 ? dA31 : dB_up;
+            rB = lane == 0 ? rA31 : rB_up;
+        }
+        if (pB == pos) {
+            idB = v;
+            dB = dv;
+            rB = rv;
+        }
+        if (lane < k && lane > pos) {
+            idA = idA_up;
+            dA = dA_up;
+            rA = rA_up;
         }
         if (lane == pos) {
-            id = v;
-            d = dv;
-            rk = rv;
+            idA = v;
+            dA = dv;
+            rA = rv;
         }
     }
-    if (lane < k) {
-        ids[(int64_t)x * k + lane] = id;
-        dd[(int64_t)x * k + lane] = d;
-        isnew[(int64_t)x * k + lane] = rk != 0;
+    if (lane < K) {
+        ids[(int64_t)x * K + lane] = lane < k ? idA : -1;
+        dd[(int64_t)x * K + lane] = lane < k ? dA : INFINITY;
+        isnew[(int64_t)x * K + lane] = lane < k && rA != 0;
     }
-    const int nnew = __popc(__ballot_sync(0xffffffffu, lane < k && rk != 0));
+    if (lane + 32 < K) {
+        ids[(int64_t)x * K + lane + 32] = lane + 32 < k ? idB : -1;
+        dd[(int64_t)x * K + lane + 32] = lane + 32 < k ? dB : INFINITY;
+        isnew[(int64_t)x * K + lane + 32] = lane + 32 < k && rB != 0;
+    }
+    const int nnew = __popc(__ballot_sync(0xffffffffu, lane < k && rA != 0)) +
+                     __popc(__ballot_sync(0xffffffffu, lane + 32 < k && rB != 0));
     if (lane == 0 && nnew) atomicAdd(delta, (unsigned long long)nnew);
 }
 
@@ -349,6 +411,11 @@ __global__ void k_edge_keys(int n, int k, const int32_t *gid, const int32_t *ids
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)n * k) return;
     const int x = (int)(e / k), y = ids[e];
+    if (y < 0) {  // unused slot: after every edge
+        keys[e] = ~0ull;
+        vals[e] = (uint32_t)e;
+        return;
+    }
     const uint32_t hsh = (uint32_t)(mix64(pair_key(gid[x], gid[y])) >> 32);
     keys[e] = ((unsigned long long)float_key(dd[e]) << 32) | hsh;
     vals[e] = (uint32_t)e;
@@ -373,12 +440,12 @@ __global__ void k_take_D(int64_t nDp, int k, const int32_t *gid, const int32_t *
 }
 
 // saturated nodes: every out-edge in D
-__global__ void k_saturated(int n, int k, const int32_t *gid, const int32_t *ids, const unsigned long long *dset,
-                            uint64_t dmask, int64_t *flag) {
+__global__ void k_saturated(int n, int k, const int32_t *klen, const int32_t *gid, const int32_t *ids,
+                            const unsigned long long *dset, uint64_t dmask, int64_t *flag) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
     bool all = true;
-    for (int r = 0; r < k && all; ++r)
+    for (int r = 0; r < klen[x] && all; ++r)
         all = set_contains(dset, dmask, pair_key(gid[x], gid[ids[(int64_t)x * k + r]]));
     flag[x] = all ? 1 : 0;
 }
@@ -698,11 +765,57 @@ recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, c
 
 // score grouped candidates (see k_score_seg); the Gaussian model scores the
 // pair list directly
+static cudaError_t launch_seg(recon_ctx *c, const int32_t *seg_node, const int64_t *seg_start, const int32_t *seg_count,
+                              const int32_t *seg_vbase, int64_t nseg, const int32_t *cand, const int32_t *gid, float *d,
+                              int threads, cudaStream_t st = nullptr) {
+    if (!st) st = c->stream;
+    if (c->model == RECON_ISING)
+        return launch_ising_score_seg(c->iv(), c->W, c->sp(), seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
+                                      gid, d, c->cnt, threads, st);
+    return launch_gauss_score_seg(c->gv(), c->W, c->sp(), seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid,
+                                  d, threads, st);
+}
+
+// The block width of the segmented scorer is picked once per context by
+// timing each candidate width on the first launch that carries enough work
+// (the kernel is idempotent, so the timing runs are ordinary launches).
+static recon_status autotune_segments(recon_ctx *c, const int32_t *seg_node, const int64_t *seg_start,
+                                      const int32_t *seg_count, const int32_t *seg_vbase, int64_t nseg,
+                                      const int32_t *cand, const int32_t *gid, float *d) {
+    const int widths[4] = {64, 128, 256, 512};
+    cudaEvent_t a, b;
+    CKS(cudaEventCreate(&a));
+    CKS(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_w = 256;
+    for (int w : widths) {
+        CKS(cudaEventRecord(a, c->stream));
+        CKS(launch_seg(c, seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid, d, w));
+        CKS(cudaEventRecord(b, c->stream));
+        CKS(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CKS(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c->tuned_threads = best_w;
+    c->stats.tuned_threads = best_w;
+    return RECON_OK;
+}
+
 recon_status score_segments_device(recon_ctx *c, const int32_t *seg_node, const int64_t *seg_start,
                                    const int32_t *seg_count, const int32_t *seg_vbase, int64_t nseg,
                                    const int32_t *cand, int64_t P, const int32_t *gid, float *d) {
     if (P <= 0) return RECON_OK;
-    if (c->model != RECON_ISING) return score_pairs_device(c, cand, P, gid, d, nullptr);
+    if (c->tuned_threads == 0 && nseg >= 256 && P >= 8 * nseg) {
+        recon_status st = autotune_segments(c, seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid, d);
+        if (st != RECON_OK) return st;
+    }
+    const int threads = c->tuned_threads ? c->tuned_threads : 256;
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (c->opt.timing) {
         for (cudaEvent_t *ev : {&ea, &eb}) {
@@ -714,8 +827,7 @@ recon_status score_segments_device(recon_ctx *c, const int32_t *seg_node, const 
         }
         CKS(cudaEventRecord(ea, c->stream));
     }
-    cudaError_t e = launch_ising_score_seg(c->iv(), c->W, c->sp(), seg_node, seg_start, seg_count, seg_vbase, nseg,
-                                           cand, gid, d, c->cnt, c->stream);
+    cudaError_t e = launch_seg(c, seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid, d, threads);
     if (e != cudaSuccess) return cuda_fail(c, e, "segmented score kernel");
     if (c->opt.timing) {
         CKS(cudaEventRecord(eb, c->stream));
@@ -766,7 +878,6 @@ static recon_status score_all_pairs(recon_ctx *c, const int32_t *gid, int64_t n,
     k_all_pairs<<<nblk(np), 256, 0, c->stream>>>(n, np, pairs);
     note_launch();
     CKS(cudaGetLastError());
-    if (c->model != RECON_ISING) return score_pairs_device(c, pairs, np, gid, d, nullptr);
     int64_t ns = 0;
     recon_status st = all_pair_segments(c, n, &ns);
     if (st != RECON_OK) return st;
@@ -838,8 +949,9 @@ static recon_status knn_exhaustive(recon_ctx *c, const int32_t *gid, int n, int 
 }
 
 // NNDescent on the node set gid[0..n) with lists of k; returns iterations
-static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k, uint64_t seed, int *iters_out,
-                                  bool learned) {
+// NNDescent over lists of capacity K with per-node lengths klen (device, n)
+static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k, const int32_t *klen,
+                                  uint64_t seed, int *iters_out, bool learned) {
     SearchBufs &S = SB(c);
     const int64_t nk = (int64_t)n * k;
     const int in_cap = k, Ucap = k + in_cap;
@@ -848,18 +960,25 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     if (learned) {
         // first level: seeds from the learned embedding, random ids for the rest
         int64_t nseeded = 0;
-        recon_status st0 = learned_seed_lists(c, n, k, seed, (int32_t *)S.knn_id.p, &nseeded);
+        recon_status st0 = learned_seed_lists(c, n, k, klen, seed, (int32_t *)S.knn_id.p, &nseeded);
         if (st0 != RECON_OK) return st0;
         c->stats.seeded_nodes = nseeded;
     } else {
-        k_knn_init<<<nblk(n), 256, 0, c->stream>>>(n, k, seed, (int32_t *)S.knn_id.p); note_launch();
+        k_knn_init<<<nblk(n), 256, 0, c->stream>>>(n, k, klen, seed, (int32_t *)S.knn_id.p); note_launch();
         CKS(cudaGetLastError());
     }
-    k_list_pairs<<<nblk(nk), 256, 0, c->stream>>>(n, k, (int32_t *)S.knn_id.p, (int32_t *)S.pairs_tmp.p); note_launch();
+    GROW(S.seg_node, sizeof(int32_t) * n);
+    GROW(S.seg_start, sizeof(int64_t) * n);
+    GROW(S.seg_count, sizeof(int32_t) * n);
+    k_list_pairs<<<nblk(nk), 256, 0, c->stream>>>(n, k, (int32_t *)S.knn_id.p, klen, (int32_t *)S.pairs_tmp.p,
+                                                  (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p,
+                                                  (int32_t *)S.seg_count.p); note_launch();
     CKS(cudaGetLastError());
-    recon_status st = score_pairs_device(c, (int32_t *)S.pairs_tmp.p, nk, gid, (float *)S.knn_d.p, nullptr);
+    recon_status st = score_segments_device(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p,
+                                            (int32_t *)S.seg_count.p, nullptr, n, (int32_t *)S.pairs_tmp.p, nk, gid,
+                                            (float *)S.knn_d.p);
     if (st != RECON_OK) return st;
-    k_sort_lists<<<nblk(n), 128, 0, c->stream>>>(n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
+    k_sort_lists<<<nblk(n, 128), 128, 0, c->stream>>>(n, k, klen, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
                                                  (uint8_t *)S.knn_new.p); note_launch();
     CKS(cudaGetLastError());
 
@@ -874,15 +993,15 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     GROW(S.scan_tmp, sizeof(int64_t) * scan_tmp_elems(n + 1));
     const int raw = Ucap * Ucap;
     int hsize = 1;
-    while (hsize < 2 * (raw + k)) hsize <<= 1;
-    const int lcap = raw;
+    while (hsize < 2 * (raw + k) && hsize < 16384) hsize <<= 1;
+    const int lcap = std::min(raw, hsize / 2);
     const size_t per_warp = sizeof(int32_t) * (size_t)(hsize + lcap + 1);
     int warps_per_block = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
     const size_t smem_gen = per_warp * warps_per_block;
     if (smem_gen > 48 * 1024)
         CKS(cudaFuncSetAttribute(k_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gen));
     // node x has at most min(raw, n-1-x) candidates
-    const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * raw, (int64_t)n * (n - 1) / 2), 1);
+    const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * lcap, (int64_t)n * (n - 1) / 2), 1);
     GROW(S.cand, sizeof(int32_t) * 2 * cand_cap);
     GROW(S.cand_d, sizeof(float) * cand_cap);
     GROW(S.seg_node, sizeof(int32_t) * n);
@@ -891,89 +1010,175 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
 
     int max_iters = c->opt.max_knn_iters;
     if (max_iters <= 0) max_iters = 2 * (int)std::ceil(std::log((double)std::max(n, 2)) / std::log(2.0 * k)) + 2;
-    int it = 0;
-    for (it = 0; it < max_iters;) {
-        ++it;
-        const uint64_t seed_it = mix64(seed ^ (0x5bd1e995ull * (uint64_t)it));
-        // 2. U
-        CKS(cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), c->stream));
-        k_in_count<<<nblk(nk), 256, 0, c->stream>>>(nk, (int32_t *)S.knn_id.p, (int32_t *)S.indeg.p); note_launch();
-        CKS(cudaGetLastError());
-        k_i32_to_i64<<<nblk(n + 1), 256, 0, c->stream>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1); note_launch();
-        CKS(cudaGetLastError());
-        CKS(launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p, c->stream));
-        CKS(cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), c->stream));
-        k_in_fill<<<nblk(nk), 256, 0, c->stream>>>(nk, (int32_t *)S.knn_id.p, (int64_t *)S.inoff.p,
-                                                   (int32_t *)S.cursor.p, (int32_t *)S.in_e.p); note_launch();
-        CKS(cudaGetLastError());
+    // offers: at most two per candidate; beyond the buffer they are dropped (counted)
+    const int64_t ocap = std::max<int64_t>(std::min<int64_t>(2 * cand_cap, (int64_t)1 << 30), 1);
+    GROW(S.off_t, sizeof(int32_t) * ocap);
+    GROW(S.off_v, sizeof(int32_t) * ocap);
+    GROW(S.off_d, sizeof(float) * ocap);
+    GROW(S.off_sv, sizeof(int32_t) * ocap);
+    GROW(S.off_sd, sizeof(float) * ocap);
+    GROW(S.iter, sizeof(int) * 4);
+    CKS(cudaMemsetAsync(S.iter.p, 0, sizeof(int) * 4, c->stream));
+    const int threads = c->tuned_threads ? c->tuned_threads : 256;
+    const unsigned stride_grid = (unsigned)std::max(1, 8 * c->num_sms);
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (c->opt.timing) {
+        CKS(cudaEventCreate(&ea));
+        CKS(cudaEventCreate(&eb));
+    }
+    // The iterations run on a private non-blocking stream (graph capture is not
+    // possible on the legacy default stream), ordered after the work already on
+    // the context's stream and before anything enqueued there afterwards.
+    const bool use_graph = c->opt.no_graphs == 0;
+    cudaStream_t gs = c->stream;
+    cudaEvent_t ev_join = nullptr;
+    if (use_graph) {
+        if (!c->gstream) CKS(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        gs = c->gstream;
+        CKS(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        CKS(cudaEventRecord(ev_join, c->stream));
+        CKS(cudaStreamWaitEvent(gs, ev_join, 0));
+    }
+    // One iteration, enqueued with every count kept on the device (so that it can
+    // be captured once as a CUDA graph and replayed); ends with one read-back of
+    // the candidate, offer and change counts and the error word.
+    // timing events inside a capture become record nodes of the graph
+    unsigned rec_flags = cudaEventRecordDefault;
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e;
+        k_next_iter<<<1, 1, 0, gs>>>((int *)S.iter.p);
+        note_launch();
+        if ((e = cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), gs))) return e;
+        k_in_count<<<nblk(nk), 256, 0, gs>>>(nk, (int32_t *)S.knn_id.p, (int32_t *)S.indeg.p);
+        note_launch();
+        k_i32_to_i64<<<nblk(n + 1), 256, 0, gs>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1);
+        note_launch();
+        if ((e = launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p,
+                                 gs)))
+            return e;
+        if ((e = cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), gs))) return e;
+        k_in_fill<<<nblk(nk), 256, 0, gs>>>(nk, (int32_t *)S.knn_id.p, (int64_t *)S.inoff.p,
+                                                   (int32_t *)S.cursor.p, (int32_t *)S.in_e.p);
+        note_launch();
         {
             const int wpb = 8;
             size_t smem = sizeof(int32_t) * 2 * Ucap * wpb;
-            k_build_U<<<nblk((int64_t)n * 32, 32 * wpb), 32 * wpb, smem, c->stream>>>(
-                n, k, in_cap, Ucap, seed_it, (int32_t *)S.knn_id.p, (uint8_t *)S.knn_new.p, (int64_t *)S.inoff.p,
-                (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
-                (int32_t *)S.Udeg.p); note_launch();
-            CKS(cudaGetLastError());
+            k_build_U<<<nblk((int64_t)n * 32, 32 * wpb), 32 * wpb, smem, gs>>>(
+                n, k, klen, in_cap, Ucap, seed, (int *)S.iter.p, (int32_t *)S.knn_id.p, (uint8_t *)S.knn_new.p,
+                (int64_t *)S.inoff.p, (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
+                (int32_t *)S.Udeg.p);
+            note_launch();
         }
-        // 3. candidates
-        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
-        k_gen<<<nblk((int64_t)n * 32, 32 * warps_per_block), 32 * warps_per_block, smem_gen, c->stream>>>(
-            n, k, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p, (int32_t *)S.knn_id.p, hsize, lcap,
-            (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt, (int32_t *)S.seg_node.p,
-            (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p); note_launch();
-        CKS(cudaGetLastError());
-        unsigned long long ncand = 0;
-        st = read_counter(c, CNT_SCRATCH0, &ncand);
-        if (st != RECON_OK) return st;
-        if ((int64_t)ncand > cand_cap) ncand = cand_cap;
-        // 4. score and offer
-        st = score_segments_device(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p,
-                                   nullptr, n, (int32_t *)S.cand.p, (int64_t)ncand, gid, (float *)S.cand_d.p);
-        if (st != RECON_OK) return st;
-        const int64_t ocap = 2 * std::max<int64_t>((int64_t)ncand, 1);
-        GROW(S.off_t, sizeof(int32_t) * ocap);
-        GROW(S.off_v, sizeof(int32_t) * ocap);
-        GROW(S.off_d, sizeof(float) * ocap);
-        GROW(S.off_sv, sizeof(int32_t) * ocap);
-        GROW(S.off_sd, sizeof(float) * ocap);
-        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH1), 0, sizeof(unsigned long long), c->stream));
-        k_offer<<<nblk((int64_t)ncand), 256, 0, c->stream>>>((int64_t)ncand, (int32_t *)S.cand.p,
-                                                             (float *)S.cand_d.p, k, (float *)S.knn_d.p,
-                                                             (int32_t *)S.off_t.p, (int32_t *)S.off_v.p,
-                                                             (float *)S.off_d.p, counter(c, CNT_SCRATCH1), ocap,
-                                                             c->cnt); note_launch();
-        CKS(cudaGetLastError());
-        unsigned long long noff = 0;
-        st = read_counter(c, CNT_SCRATCH1, &noff);
-        if (st != RECON_OK) return st;
-        if ((int64_t)noff > ocap) noff = ocap;
-        // group offers by target
-        CKS(cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), c->stream));
-        k_count_targets<<<nblk((int64_t)noff), 256, 0, c->stream>>>((int64_t)noff, (int32_t *)S.off_t.p,
-                                                                    (int32_t *)S.indeg.p); note_launch();
-        CKS(cudaGetLastError());
-        k_i32_to_i64<<<nblk(n + 1), 256, 0, c->stream>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1); note_launch();
-        CKS(cudaGetLastError());
-        CKS(launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p, c->stream));
-        CKS(cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), c->stream));
-        k_scatter_offers<<<nblk((int64_t)noff), 256, 0, c->stream>>>(
-            (int64_t)noff, (int32_t *)S.off_t.p, (int32_t *)S.off_v.p, (float *)S.off_d.p, (int64_t *)S.inoff.p,
-            (int32_t *)S.cursor.p, (int32_t *)S.off_sv.p, (float *)S.off_sd.p); note_launch();
-        CKS(cudaGetLastError());
-        // 5. merge
-        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH2), 0, sizeof(unsigned long long), c->stream));
-        k_merge<<<nblk((int64_t)n * 32), 256, 0, c->stream>>>(n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
-                                                               (uint8_t *)S.knn_new.p, (int64_t *)S.inoff.p,
-                                                               (int32_t *)S.off_sv.p, (float *)S.off_sd.p,
-                                                               counter(c, CNT_SCRATCH2)); note_launch();
-        CKS(cudaGetLastError());
-        unsigned long long delta = 0;
-        st = read_counter(c, CNT_SCRATCH2, &delta);
-        if (st != RECON_OK) return st;
-        st = check_err_flags(c, "NNDescent");
-        if (st != RECON_OK) return st;
-        if ((double)delta / ((double)k * n) < c->opt.eps_knn) break;
+        if ((e = cudaMemsetAsync(c->cnt + CNT_SCRATCH0, 0, sizeof(unsigned long long) * 4, gs))) return e;
+        k_gen<<<nblk((int64_t)n * 32, 32 * warps_per_block), 32 * warps_per_block, smem_gen, gs>>>(
+            n, k, klen, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p, (int32_t *)S.knn_id.p, hsize,
+            lcap, (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt, (int32_t *)S.seg_node.p,
+            (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p);
+        note_launch();
+        if (ea && (e = cudaEventRecordWithFlags(ea, gs, rec_flags))) return e;
+        if ((e = launch_seg(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p, nullptr,
+                            n, (int32_t *)S.cand.p, gid, (float *)S.cand_d.p, threads, gs)))
+            return e;
+        if (eb && (e = cudaEventRecordWithFlags(eb, gs, rec_flags))) return e;
+        k_offer<<<stride_grid, 256, 0, gs>>>(counter(c, CNT_SCRATCH0), cand_cap, (int32_t *)S.cand.p,
+                                                    (float *)S.cand_d.p, k, klen, (float *)S.knn_d.p,
+                                                    (int32_t *)S.off_t.p, (int32_t *)S.off_v.p, (float *)S.off_d.p,
+                                                    counter(c, CNT_SCRATCH1), ocap, counter(c, CNT_SCRATCH3));
+        note_launch();
+        if ((e = cudaMemsetAsync(S.indeg.p, 0, sizeof(int32_t) * (n + 1), gs))) return e;
+        k_count_targets<<<stride_grid, 256, 0, gs>>>(counter(c, CNT_SCRATCH1), ocap, (int32_t *)S.off_t.p,
+                                                            (int32_t *)S.indeg.p);
+        note_launch();
+        k_i32_to_i64<<<nblk(n + 1), 256, 0, gs>>>((int32_t *)S.indeg.p, (int64_t *)S.scan_in.p, n + 1);
+        note_launch();
+        if ((e = launch_scan_i64((int64_t *)S.scan_in.p, (int64_t *)S.inoff.p, n + 1, (int64_t *)S.scan_tmp.p,
+                                 gs)))
+            return e;
+        if ((e = cudaMemsetAsync(S.cursor.p, 0, sizeof(int32_t) * (n + 1), gs))) return e;
+        k_scatter_offers<<<stride_grid, 256, 0, gs>>>(counter(c, CNT_SCRATCH1), ocap, (int32_t *)S.off_t.p,
+                                                             (int32_t *)S.off_v.p, (float *)S.off_d.p,
+                                                             (int64_t *)S.inoff.p, (int32_t *)S.cursor.p,
+                                                             (int32_t *)S.off_sv.p, (float *)S.off_sd.p);
+        note_launch();
+        k_merge<<<nblk((int64_t)n * 32), 256, 0, gs>>>(n, k, klen, gid, (int32_t *)S.knn_id.p,
+                                                              (float *)S.knn_d.p, (uint8_t *)S.knn_new.p,
+                                                              (int64_t *)S.inoff.p, (int32_t *)S.off_sv.p,
+                                                              (float *)S.off_sd.p, counter(c, CNT_SCRATCH2));
+        note_launch();
+        // counts back to the host: candidates, offers, changes, drops; and the error word
+        if ((e = cudaMemcpyAsync(c->cnt_host + CNT_SCRATCH0, c->cnt + CNT_SCRATCH0, sizeof(unsigned long long) * 4,
+                                 cudaMemcpyDeviceToHost, gs)))
+            return e;
+        if ((e = cudaMemcpyAsync(c->cnt_host + CNT_ERR, c->cnt + CNT_ERR, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, gs)))
+            return e;
+        return cudaGetLastError();
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+        // a capture that fails leaves the launch-by-launch path in use
+        cudaGraph_t graph = nullptr;
+        const int64_t launches0 = c->stats.kernel_launches;
+        cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rec_flags = cudaEventRecordExternal;
+            cudaError_t ce = enqueue();
+            rec_flags = cudaEventRecordDefault;
+            cudaError_t ee = cudaStreamEndCapture(gs, &graph);
+            e = ce != cudaSuccess ? ce : ee;
+        }
+        c->graph_launches_per_iter = c->stats.kernel_launches - launches0;
+        c->stats.kernel_launches = launches0;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            exec = nullptr;
+            cudaGetLastError();
+        }
     }
+    int it = 0;
+    recon_status result = RECON_OK;
+    for (it = 0; it < max_iters;) {
+        ++it;
+        cudaError_t e;
+        if (exec) {
+            e = cudaGraphLaunch(exec, gs);
+            c->stats.kernel_launches += c->graph_launches_per_iter;
+        } else
+            e = enqueue();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+        if (e != cudaSuccess) {
+            result = cuda_fail(c, e, "NNDescent iteration");
+            break;
+        }
+        const unsigned long long ncand = std::min<unsigned long long>(c->cnt_host[CNT_SCRATCH0], cand_cap);
+        const unsigned long long delta = c->cnt_host[CNT_SCRATCH2];
+        c->stats.pair_evals += (int64_t)ncand;
+        c->stats.dropped_offers += (int64_t)c->cnt_host[CNT_SCRATCH3];
+        if (ea) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ea, eb) == cudaSuccess) {
+                c->stats.score_ms += ms;
+                c->stats.score_launches += 1;
+                c->stats.score_pairs += (int64_t)ncand;
+            } else
+                cudaGetLastError();
+        }
+        if (c->cnt_host[CNT_ERR]) {
+            result = check_err_flags(c, "NNDescent");
+            if (result != RECON_OK) break;
+        }
+        if ((double)delta / (double)S.klen_sum < c->opt.eps_knn) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev_join) {
+        cudaEventRecord(ev_join, gs);
+        cudaStreamWaitEvent(c->stream, ev_join, 0);
+        cudaEventDestroy(ev_join);
+    }
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+    if (result != RECON_OK) return result;
     *iters_out = it;
     return RECON_OK;
 }
@@ -1041,8 +1246,19 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
     int64_t n = N;
     const uint64_t call_seed = mix64(c->opt.seed ^ mix64(0x9e37ull + (uint64_t)c->stats_calls));
     c->stats_calls++;
+    S.g0_n = N;
+    S.g0_K = 0;
+    S.g0_moved = false;
     for (int level = 0;; ++level) {
         if (level < 17) c->stats.level_size[level] = n;
+        if (level == 1 && S.g0_K > 0) {
+            // keep the first level's lists (the k-NN graph of all nodes): the
+            // buffers change places, nothing is copied
+            std::swap(S.knn_id, S.g0_id);
+            std::swap(S.knn_d, S.g0_d);
+            std::swap(S.klen, S.g0_klen);
+            S.g0_moved = true;
+        }
         if (n * n <= 4 * m) {
             recon_status st = exhaustive_best_set(c, level == 0 ? nullptr : gid, n, m);
             if (st != RECON_OK) return st;
@@ -1051,19 +1267,41 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
         int64_t k64 = (4 * m + n - 1) / n;
         k64 = std::max<int64_t>(k64, k_cfg);
         k64 = std::min<int64_t>(k64, n - 1);
-        const int k = (int)k64;
+        int k = (int)k64;
+        // per-node list lengths (first level only, when the caller set them)
+        const bool uneven = level == 0 && (int64_t)c->klen_host.size() == n;
+        GROW(S.klen, sizeof(int32_t) * n);
+        if (uneven) {
+            std::vector<int32_t> kl(n);
+            int kmax = 1;
+            int64_t sum = 0;
+            for (int64_t x = 0; x < n; ++x) {
+                kl[x] = (int32_t)std::min<int64_t>(n - 1, std::max<int64_t>(c->klen_host[x], (4 * m + n - 1) / n));
+                kmax = std::max(kmax, (int)kl[x]);
+                sum += kl[x];
+            }
+            if (kmax > NND_MAX_K)
+                return set_err(c, RECON_EUNSUPPORTED, "per-node list lengths above %d", NND_MAX_K);
+            CKS(cudaMemcpyAsync(S.klen.p, kl.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream));
+            CKS(cudaStreamSynchronize(c->stream));
+            k = kmax;
+            S.klen_sum = sum;
+        } else {
+            CKS(launch_fill_i32((int32_t *)S.klen.p, k, n, c->stream));
+            S.klen_sum = n * (int64_t)k;
+        }
         if (level < 16) c->stats.level_k[level] = k;
         c->stats.levels = level + 1;
         const int64_t nk = n * k;
         GROW(S.knn_id, sizeof(int32_t) * nk);
         GROW(S.knn_d, sizeof(float) * nk);
         GROW(S.knn_new, sizeof(uint8_t) * nk);
-        bool exhaustive = c->opt.knn_mode == RECON_KNN_EXHAUSTIVE || k > NND_MAX_K;
+        bool exhaustive = (c->opt.knn_mode == RECON_KNN_EXHAUSTIVE || k > NND_MAX_K) && !uneven;
         if (c->opt.knn_mode == RECON_KNN_AUTO) {
             // NNDescent scores about |S| (2k)^2 / 2 pairs per iteration
             double nnd = (double)n * 4.0 * k * k / 2.0 * 3.0;
             double exh = (double)n * (n - 1) / 2.0;
-            exhaustive = exhaustive || exh <= nnd;
+            exhaustive = (exhaustive || exh <= nnd) && !uneven;
         }
         if (exhaustive && (double)n * n * 4.0 > 16e9)
             return set_err(c, RECON_EUNSUPPORTED, "level of %lld nodes with k = %d needs NNDescent with k <= %d",
@@ -1074,10 +1312,12 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
         } else {
             int iters = 0;
             const bool learned = level == 0 && c->opt.seed_mode == RECON_SEED_LEARNED && c->prop && c->prop->trained;
-            st = knn_nndescent(c, gid, (int)n, k, mix64(call_seed + (uint64_t)level), &iters, learned);
+            st = knn_nndescent(c, gid, (int)n, k, (int32_t *)S.klen.p, mix64(call_seed + (uint64_t)level), &iters,
+                               learned);
             c->stats.knn_iters += iters;
         }
         if (st != RECON_OK) return st;
+        if (level == 0) S.g0_K = k;
         // D+ : the 2m best directed edges
         GROW(S.ek, sizeof(unsigned long long) * nk);
         GROW(S.ev, sizeof(uint32_t) * nk);
@@ -1086,7 +1326,7 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
         CKS(cudaGetLastError());
         st = sort_kv(c, (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p, nk, 0, 64);
         if (st != RECON_OK) return st;
-        const int64_t nDp = std::min<int64_t>(2 * m, nk);
+        const int64_t nDp = std::min<int64_t>(2 * m, S.klen_sum);
         // D : unique pairs of D+
         uint64_t dcap = 1;
         while (dcap < (uint64_t)(4 * nDp + 64)) dcap <<= 1;
@@ -1108,7 +1348,7 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
         GROW(S.flag, sizeof(int64_t) * (n + 1));
         GROW(S.pos, sizeof(int64_t) * (n + 1));
         GROW(S.scan_tmp2, sizeof(int64_t) * scan_tmp_elems(n + 1));
-        k_saturated<<<nblk(n), 256, 0, c->stream>>>((int)n, k, gid, (int32_t *)S.knn_id.p,
+        k_saturated<<<nblk(n), 256, 0, c->stream>>>((int)n, k, (int32_t *)S.klen.p, gid, (int32_t *)S.knn_id.p,
                                                     (unsigned long long *)S.dset.p, dcap - 1, (int64_t *)S.flag.p); note_launch();
         CKS(cudaGetLastError());
         CKS(cudaMemsetAsync((int64_t *)S.flag.p + n, 0, sizeof(int64_t), c->stream));
@@ -1141,6 +1381,7 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
 recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count) {
     SearchBufs &S = SB(c);
     S.res_n = 0;
+    S.g0_K = 0;
     const int64_t N = c->N, K = 2 * c->Mp;
     GROW(S.scr_A, sizeof(uint16_t) * (size_t)N * K);
     GROW(S.scr_B, sizeof(uint16_t) * (size_t)N * K);
@@ -1224,5 +1465,38 @@ recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float 
     if (st != RECON_OK) return st;
     *pairs_dev = (int32_t *)S.out_pairs.p;
     *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}
+
+// the first level's lists of the last FindBest search, with global node ids
+recon_status knn_graph_copy(recon_ctx *c, int32_t *ids, float *d, int64_t cap, int32_t *k_out, int64_t *n_out) {
+    SearchBufs &S = SB(c);
+    const int K = S.g0_K;
+    const int64_t n = K > 0 ? S.g0_n : 0;
+    if (k_out) *k_out = K;
+    if (n_out) *n_out = n;
+    if (!ids && !d) return RECON_OK;
+    if (cap < n * K) return set_err(c, RECON_EINVAL, "cap %lld < N k = %lld", (long long)cap, (long long)(n * K));
+    if (n == 0) return RECON_OK;
+    const DBuf &bi = S.g0_moved ? S.g0_id : S.knn_id;
+    const DBuf &bd = S.g0_moved ? S.g0_d : S.knn_d;
+    std::vector<int32_t> hi((size_t)(n * K));
+    std::vector<float> hd((size_t)(n * K));
+    CKS(cudaMemcpyAsync(hi.data(), bi.p, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, c->stream));
+    CKS(cudaMemcpyAsync(hd.data(), bd.p, sizeof(float) * n * K, cudaMemcpyDeviceToHost, c->stream));
+    CKS(cudaStreamSynchronize(c->stream));
+    // NNDescent keeps its rows ascending; the exhaustive k-NN selection does
+    // not order them, so rows are put in ascending d here (stable)
+    std::vector<int> perm(K);
+    for (int64_t x = 0; x < n; ++x) {
+        const float *dr = hd.data() + x * K;
+        const int32_t *ir = hi.data() + x * K;
+        for (int r = 0; r < K; ++r) perm[r] = r;
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return dr[a] < dr[b]; });
+        for (int r = 0; r < K; ++r) {
+            if (ids) ids[x * K + r] = ir[perm[r]];
+            if (d) d[x * K + r] = dr[perm[r]];
+        }
+    }
     return RECON_OK;
 }

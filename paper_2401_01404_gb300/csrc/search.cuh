@@ -24,14 +24,23 @@ struct SearchBufs {
     DBuf out_pairs, out_d;                        // result
     DBuf sort_k2, sort_v2, sort_tmp;              // radix sort scratch
     DBuf scr_A, scr_B, scr_l1;                    // screen operands
+    DBuf klen;                                    // per-node list lengths of the current level
+    DBuf iter;                                    // device-side iteration counter
+    DBuf g0_id, g0_d, g0_klen;                    // first-level lists, kept when a later level runs
     int64_t res_n = 0;
+    int64_t klen_sum = 0;
+    // the k-NN graph of the first level: rows g0_n, stride g0_K (0: no lists);
+    // g0_moved: the lists were moved into g0_* when the second level started
+    int64_t g0_n = 0;
+    int g0_K = 0;
+    bool g0_moved = false;
 
     std::vector<DBuf *> all() {
         return {&knn_id, &knn_d, &knn_new, &indeg, &inoff, &cursor, &in_e, &U, &Uf, &Udeg,
                 &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &seg_node, &seg_start, &seg_count, &seg_vbase, &off_t, &off_v, &off_d, &off_sv,
                 &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
                 &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
-                &out_d, &sort_k2, &sort_v2, &sort_tmp, &scr_A, &scr_B, &scr_l1};
+                &out_d, &sort_k2, &sort_v2, &sort_tmp, &scr_A, &scr_B, &scr_l1, &klen, &iter, &g0_id, &g0_d, &g0_klen};
     }
 };
 
@@ -41,3 +50,4 @@ recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, c
 recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
 recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
 recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
+recon_status knn_graph_copy(recon_ctx *c, int32_t *ids, float *d, int64_t cap, int32_t *k_out, int64_t *n_out);

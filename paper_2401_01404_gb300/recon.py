@@ -28,7 +28,8 @@ class recon_options(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("seed", C.c_uint64), ("eps_knn", C.c_double),
                 ("max_knn_iters", C.c_int32), ("w_clamp", C.c_float), ("h_clamp", C.c_float),
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
-                ("timing", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("timing", C.c_int32), ("no_graphs", C.c_int32),
+                ("learned_frac", C.c_float), ("reserved", C.c_int32 * 5)]
 
 
 class recon_stats(C.Structure):
@@ -37,7 +38,8 @@ class recon_stats(C.Structure):
                 ("nnz", C.c_int64), ("samples", C.c_int64), ("kernel_launches", C.c_int64),
                 ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double),
                 ("screen_launches", C.c_int64), ("screen_ms", C.c_double), ("screen_flop", C.c_double),
-                ("screen_survivors", C.c_int64), ("seeded_nodes", C.c_int64)]
+                ("screen_survivors", C.c_int64), ("seeded_nodes", C.c_int64), ("tuned_threads", C.c_int64),
+                ("dropped_offers", C.c_int64)]
 
 
 class recon_train_opts(C.Structure):
@@ -72,6 +74,8 @@ _EXPORTS = {
     "recon_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
     "recon_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "recon_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
+    "recon_set_list_lengths": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "recon_knn_graph": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "recon_proposal_param_count": (C.c_int64, []),
     "recon_default_train_opts": (None, [C.c_void_p]),
     "recon_proposal_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -257,7 +261,30 @@ def recon_get_stats(ctx) -> dict:
             "kernel_launches": s.kernel_launches, "score_launches": s.score_launches,
             "score_pairs": s.score_pairs, "score_ms": s.score_ms, "screen_launches": s.screen_launches,
             "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors,
-            "seeded_nodes": s.seeded_nodes}
+            "seeded_nodes": s.seeded_nodes, "tuned_threads": s.tuned_threads,
+            "dropped_offers": s.dropped_offers}
+
+
+def recon_set_list_lengths(ctx, k=None):
+    """Per-node list lengths of the first FindBest level (None clears them)."""
+    if k is None:
+        _check(lib().recon_set_list_lengths(ctx, None, 0), ctx)
+        return
+    a = np.ascontiguousarray(np.asarray(k, dtype=np.int32))
+    _check(lib().recon_set_list_lengths(ctx, a.ctypes.data, len(a)), ctx)
+
+
+def recon_knn_graph(ctx):
+    """The first-level k-NN lists of the last FindBest search: (ids [N x k],
+    d [N x k]), padding id -1 / d +inf; empty arrays when no lists were built."""
+    k = C.c_int32(0)
+    n = C.c_int64(0)
+    _check(lib().recon_knn_graph(ctx, None, None, 0, C.byref(k), C.byref(n)), ctx)
+    ids = np.empty((n.value, k.value), dtype=np.int32)
+    d = np.empty((n.value, k.value), dtype=np.float32)
+    if ids.size:
+        _check(lib().recon_knn_graph(ctx, ids.ctypes.data, d.ctypes.data, ids.size, C.byref(k), C.byref(n)), ctx)
+    return ids, d
 
 
 def recon_proposal_param_count() -> int:
@@ -357,6 +384,9 @@ class Recon:
 
     def best_pairs(self, k: int, kappa: float):
         return recon_best_pairs(self.ctx, k, kappa, self.N)
+
+    def knn_graph(self):
+        return recon_knn_graph(self.ctx)
 
     def exhaustive_best(self, m: int):
         return recon_exhaustive_best(self.ctx, m, self.N)

@@ -2,7 +2,8 @@
 FP64 oracle (which is pinned by finite differences), training on exact pair
 scores lowers the loss, and seeding the first NNDescent lists from the trained
 embedding finds more of the exact best pairs after one iteration than random
-seeding on the same data."""
+seeding on the same data; the recall curves with and without the proposal are
+reported on equal seeds."""
 import math
 
 import numpy as np
@@ -73,8 +74,9 @@ def test_training_lowers_the_loss_and_seeding_helps(R):
     assert loss[-1] < 0.5 * loss[0]
     w = R.recon_proposal_weights(trainer.ctx)
 
-    def recall_after(seed_mode, iters):
-        c = R.Recon(Xs, R.RECON_ISING, lam=lam, seed_mode=seed_mode, max_knn_iters=iters, eps_knn=0.0, seed=11)
+    def recall_after(seed_mode, iters, seed, frac=0.5):
+        c = R.Recon(Xs, R.RECON_ISING, lam=lam, seed_mode=seed_mode, max_knn_iters=iters, eps_knn=0.0, seed=seed,
+                    learned_frac=frac)
         if seed_mode == R.RECON_SEED_LEARNED:
             R.recon_proposal_weights(c.ctx, w)  # the weights trained on the other context
         p, _ = c.best_pairs(16, kappa)
@@ -82,7 +84,18 @@ def test_training_lowers_the_loss_and_seeding_helps(R):
         c.close()
         return len(truth & {tuple(x) for x in p.tolist()}) / len(truth), st
 
-    r_rand, _ = recall_after(R.RECON_SEED_RANDOM, 1)
-    r_learn, st = recall_after(R.RECON_SEED_LEARNED, 1)
+    # recall after 1, 2 and 6 iterations with and without the proposal, equal seeds
+    seeds = (11, 12, 13)
+    curves = {}
+    for name, mode, frac in (("random", R.RECON_SEED_RANDOM, 0.5), ("learned f=0.5", R.RECON_SEED_LEARNED, 0.5),
+                             ("learned f=1", R.RECON_SEED_LEARNED, 1.0)):
+        curves[name] = {it: [recall_after(mode, it, s, frac)[0] for s in seeds] for it in (1, 2, 6)}
+        print(name, {it: np.round(v, 4).tolist() for it, v in curves[name].items()})
+    _, st = recall_after(R.RECON_SEED_LEARNED, 1, 11, 1.0)
     assert st["seeded_nodes"] > N // 2
-    assert r_learn > r_rand + 0.05, (r_learn, r_rand)
+    # lists seeded entirely from the proposal hold more of the best pairs after
+    # the first iteration (mean over the seeds) ...
+    assert np.mean(curves["learned f=1"][1]) > np.mean(curves["random"][1]) + 0.01, curves
+    # ... and every seeding converges (random ids keep the search exploring)
+    for name in curves:
+        assert np.mean(curves[name][6]) > 0.97, (name, curves[name][6])
