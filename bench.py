@@ -45,6 +45,10 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scale-workload", default=None,
+                    help="also measure time to 0.99 recall on this large workload (subsample ground truth)")
+    ap.add_argument("--scale-rows", type=int, default=10000)
+    ap.add_argument("--scale-caps", type=int, default=8)
     return ap.parse_args()
 
 
@@ -100,9 +104,11 @@ def _workload(name, rank, device):
     wl = inputs.config(name, device=device)
     if rank:
         # independent replica per rank: a new sample draw of the same planted model
+        lam = wl.lam
         wl = inputs.ising_workload(name, wl.N, wl.M, "regular" if "n2000" in name else "er",
                                    4 if "n2000" in name else 5, "pm" if "n2000" in name else "normal",
                                    0.3, 0.0, 1000, 2000 + 7919 * rank, wl.k, wl.kappa, device)
+        wl.lam = lam
     return wl
 
 
@@ -222,6 +228,93 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
     return out
 
 
+def _scale_recall(R, name, stream, rows_n, max_cap):
+    """Time to 0.99 best-pair recall on a workload too large for an exhaustive
+    ground truth.  Truth: a seeded subsample S of nodes, every pair incident to
+    S scored against all N columns (recon_row_best); recall = found best pairs
+    incident to S against the exact best pairs incident to S under the global
+    cut.  The cut is the m-th best d of the exact screen, itself checked on S;
+    a cut estimated from S alone is reported beside it."""
+    import torch
+    from paper_2401_01404_gb300 import inputs
+
+    out = {"workload": name}
+    t = time.perf_counter()
+    wl = inputs.config(name, device="cuda")
+    out["generation_s"] = round(time.perf_counter() - t, 2)
+    N, M, k, kappa = wl.N, wl.M, wl.k, wl.kappa
+    m = int(math.floor(kappa * N + 0.5))
+    lam = wl.lam
+    out.update({"N": N, "M": M, "k": k, "kappa": kappa, "m": m, "lambda": round(lam, 4)})
+    X_dev = torch.from_numpy(wl.samples_major()).cuda()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    # chosen: the exact screen (bf16 tensor cores + FP32 re-scoring)
+    scr = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    scr.best_pairs(k, kappa)
+    s0 = scr.stats()
+    (p_scr, d_scr), t_scr = timed(lambda: scr.best_pairs(k, kappa))
+    s1 = scr.stats()
+    dflop, dms = s1["screen_flop"] - s0["screen_flop"], s1["screen_ms"] - s0["screen_ms"]
+    out["chosen_s"] = t_scr
+    out["screen"] = {"tflops": dflop / (dms / 1e3) / 1e12 if dms else None, "ms": dms,
+                     "survivors": s1["screen_survivors"] - s0["screen_survivors"]}
+    cut = float(d_scr[-1])
+    # truth on the subsample
+    S = np.sort(inputs.rng(5 + N, inputs.STATE).choice(N, rows_n, replace=False))
+    (tp, td, tn), t_truth = timed(lambda: scr.row_best(S, cut))
+    truth = {tuple(x) for x in tp.tolist()}
+    out["truth"] = {"rows": rows_n, "pairs": len(truth), "seconds": t_truth, "cut_d": cut}
+    # the cut estimated from S alone: pairs incident to S are a 2|S|/N share of all
+    q = int(round(2.0 * m * rows_n / N))
+    pp, dd, nn = scr.row_best(S, 0.0)
+    out["truth"]["cut_d_estimated_from_rows"] = float(dd[min(q, len(dd)) - 1]) if len(dd) else None
+    inS = np.zeros(N, dtype=bool)
+    inS[S] = True
+
+    def recall(p):
+        sel = p[inS[p[:, 0]] | inS[p[:, 1]]]
+        return len(truth & {tuple(x) for x in sel.tolist()}) / max(len(truth), 1)
+
+    out["chosen_recall"] = recall(p_scr)
+    scr.close()
+    # learned proposal: pretrained on a 10^5-node draw of the same planted model
+    t = time.perf_counter()
+    pre = inputs.ising_workload(name + "_pretrain", 100000, M, "er", 5, "normal", 0.3, 0.0, 300, 4243, k, kappa, "cuda")
+    tr = R.Recon(pre.samples_major(), R.RECON_ISING, stream=stream, lam=inputs.default_lambda(100000, M, 2.0))
+    losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
+    weights = R.recon_proposal_weights(tr.ctx)
+    tr.close()
+    out["pretrain"] = {"seconds": round(time.perf_counter() - t, 2), "N": 100000, "loss_first": float(losses[0]),
+                       "loss_last": float(losses[-1])}
+    for tag, mode in (("plain_fp32", R.RECON_SEED_RANDOM), ("learned_fp32", R.RECON_SEED_LEARNED)):
+        curve, t_hit = [], None
+        for cap in range(1, max_cap + 1):
+            ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
+                          seed_mode=mode)
+            if mode == R.RECON_SEED_LEARNED:
+                R.recon_proposal_weights(ctx.ctx, weights)
+            ctx.best_pairs(k, kappa)  # allocates the buffers
+            (p, d), dt = timed(lambda: ctx.best_pairs(k, kappa))
+            st = ctx.stats()
+            ctx.close()
+            rec = recall(p)
+            curve.append((cap, round(dt, 4), round(rec, 5), int(st["dropped_offers"])))
+            if rec >= 0.99:
+                t_hit = dt
+                break
+        out[tag + "_s"] = t_hit
+        out[tag + "_curve"] = curve
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(a):
@@ -243,7 +336,7 @@ def run_ours(a):
     wl = _workload(a.workload, rank, "cuda")
     k = a.k or wl.k
     kappa = a.kappa or wl.kappa
-    lam = inputs.default_lambda(wl.N, wl.M)
+    lam = wl.lam
     stream = torch.cuda.current_stream()
     X_host = torch.from_numpy(wl.samples_major()).pin_memory()
     X_dev = X_host.cuda()
@@ -356,6 +449,8 @@ def run_ours(a):
                                          "unit": "TFLOP/s", "frac": ttr["screen"]["tflops"] / bf16,
                                          "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
         line["time_to_recall"] = ttr
+    if a.scale_workload and rank == 0:
+        line["time_to_recall_scale"] = _scale_recall(R, a.scale_workload, stream, a.scale_rows, a.scale_caps)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -372,7 +467,7 @@ def run_reference(a):
 
     oracle.build()
     wl = inputs.config(a.workload, device="cpu")
-    lam = inputs.default_lambda(wl.N, wl.M)
+    lam = wl.lam
     h = oracle.ising_fields_at_zero(wl.X)
     phi = np.repeat(h[:, None], wl.M, 1)
     P = 2048

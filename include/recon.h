@@ -211,6 +211,17 @@ recon_status recon_set_list_lengths(recon_ctx *ctx, const int32_t *k, int64_t n)
  * queries the sizes.  EINVAL if cap < N k. Synchronous. */
 recon_status recon_knn_graph(recon_ctx *ctx, int32_t *ids, float *d, int64_t cap, int32_t *k_out, int64_t *n_out);
 
+/* recon_row_best -- every pair {i, j} with i in rows, j != i and d(i, j) < d_cut,
+ * scored exactly at the current state (as recon_score) against all N columns of
+ * each row: Algorithm 3's exhaustive scoring restricted to a node subset, the
+ * ground truth of a subsample (rows on the host, duplicates allowed, each in
+ * [0, N)).  The pairs are canonical (i < j), unique, in ascending (d, i, j);
+ * the first min(count, cap) are written to the host buffers pairs [cap x 2] and
+ * d [cap] (d may be NULL); *count_out = the number found.  Costs N scores per
+ * row.  EINVAL on a bad row, a NaN cut, or cap > 0 with pairs NULL. Synchronous. */
+recon_status recon_row_best(recon_ctx *ctx, const int32_t *rows, int64_t nrows, float d_cut, int32_t *pairs, float *d,
+                            int64_t cap, int64_t *count_out);
+
 /* recon_exhaustive_best -- the m best pairs over all N(N-1)/2 pairs, exact
  * (Algorithm 3's exhaustive base case applied to the whole node set); the
  * ground truth that recall is measured against.  Arguments as in

@@ -414,6 +414,30 @@ extern "C" recon_status recon_exhaustive_best(recon_ctx *c, int64_t m, int32_t *
     return RECON_OK;
 }
 
+extern "C" recon_status recon_row_best(recon_ctx *c, const int32_t *rows, int64_t nrows, float d_cut, int32_t *pairs,
+                                       float *d, int64_t cap, int64_t *count_out) {
+    LIVE(c);
+    if (!count_out) return set_err(c, RECON_EINVAL, "count_out is NULL");
+    *count_out = 0;
+    if (nrows < 0 || (nrows > 0 && !rows)) return set_err(c, RECON_EINVAL, "rows");
+    if (cap < 0 || (cap > 0 && !pairs)) return set_err(c, RECON_EINVAL, "pairs / cap");
+    if (std::isnan(d_cut)) return set_err(c, RECON_EINVAL, "d_cut is NaN");
+    for (int64_t r = 0; r < nrows; ++r)
+        if (rows[r] < 0 || rows[r] >= c->N) return set_err(c, RECON_EINVAL, "row %lld = %d outside [0, N)", (long long)r, rows[r]);
+    if (nrows == 0 || c->N < 2) return RECON_OK;
+    ENSURE(BUF_TMP2, sizeof(int32_t) * nrows);
+    CK(cudaMemcpyAsync(c->bufs[BUF_TMP2].p, rows, sizeof(int32_t) * nrows, cudaMemcpyHostToDevice, c->stream));
+    int32_t *pd = nullptr;
+    float *dd = nullptr;
+    int64_t n = 0;
+    recon_status st = row_best_run(c, buf<int32_t>(c, BUF_TMP2), nrows, d_cut, &pd, &dd, &n);
+    if (st != RECON_OK) return st;
+    st = deliver_pairs(c, pd, dd, std::min(n, cap), pairs, d, 0);
+    if (st != RECON_OK) return st;
+    *count_out = n;
+    return RECON_OK;
+}
+
 // the update loop over a device pair list (already checked)
 static recon_status cd_sweep_dev(recon_ctx *c, const int32_t *dp, int64_t P, double *delta_out) {
     if (P == 0) {

@@ -19,6 +19,9 @@
 //      entries that are new.
 // The loop stops when Delta/(k|S|) < eps or after the iteration cap.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 
 #include "common.cuh"
@@ -812,8 +815,25 @@ recon_status score_segments_device(recon_ctx *c, const int32_t *seg_node, const 
                                    const int32_t *cand, int64_t P, const int32_t *gid, float *d) {
     if (P <= 0) return RECON_OK;
     if (c->tuned_threads == 0 && nseg >= 256 && P >= 8 * nseg) {
-        recon_status st = autotune_segments(c, seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid, d);
-        if (st != RECON_OK) return st;
+        // the width is a property of the kernel, the device and the row length:
+        // tuned once per process for each (device, model, Mp)
+        static std::mutex mu;
+        static std::map<std::tuple<int, int, int64_t>, int> tuned;
+        const auto key = std::make_tuple(c->device, c->model, c->Mp);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            auto it = tuned.find(key);
+            if (it != tuned.end()) {
+                c->tuned_threads = it->second;
+                c->stats.tuned_threads = it->second;
+            }
+        }
+        if (c->tuned_threads == 0) {
+            recon_status st = autotune_segments(c, seg_node, seg_start, seg_count, seg_vbase, nseg, cand, gid, d);
+            if (st != RECON_OK) return st;
+            std::lock_guard<std::mutex> lk(mu);
+            tuned[key] = c->tuned_threads;
+        }
     }
     const int threads = c->tuned_threads ? c->tuned_threads : 256;
     cudaEvent_t ea = nullptr, eb = nullptr;
@@ -1462,6 +1482,106 @@ recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float 
     recon_status st = exhaustive_best_set(c, nullptr, c->N, m);
     if (st != RECON_OK) return st;
     st = finish_results(c, m, count);
+    if (st != RECON_OK) return st;
+    *pairs_dev = (int32_t *)S.out_pairs.p;
+    *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}
+
+// segments of whole rows: row r of the batch covers columns [0, n) in chunks
+// of 512, d of (rows[r], y) at r n + y
+__global__ void k_row_segments(int64_t nb, int64_t n, int64_t nch, const int32_t *rows, int32_t *seg_node,
+                               int64_t *seg_start, int32_t *seg_count, int32_t *seg_vbase) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nb * nch) return;
+    const int64_t r = s / nch, ch = s % nch;
+    const int64_t y0 = ch * 512;
+    seg_node[s] = rows[r];
+    seg_start[s] = r * n + y0;
+    seg_count[s] = (int32_t)min((int64_t)512, n - y0);
+    seg_vbase[s] = (int32_t)y0;
+}
+
+// pairs {rows[r], y}, y != rows[r], with d < cut, appended in canonical order
+__global__ void k_row_select(int64_t nb, int64_t n, const int32_t *rows, const float *dd, float cut, int32_t *pairs,
+                             float *dout, int64_t cap, unsigned long long *counter) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = e < nb * n;
+    int x = 0, y = 0;
+    float d = 0.f;
+    bool take = false;
+    if (in) {
+        x = rows[e / n];
+        y = (int)(e % n);
+        d = dd[e];
+        take = y != x && d < cut;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, take);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!take) return;
+    const int64_t q = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+    if (q >= cap) return;
+    pairs[2 * q] = min(x, y);
+    pairs[2 * q + 1] = max(x, y);
+    dout[q] = d;
+}
+
+// every pair incident to the given rows with d < cut, scored exactly (all N
+// columns of each row), unique and ordered by (d, i, j): Algorithm 3's
+// exhaustive scoring restricted to a node subset
+recon_status row_best_run(recon_ctx *c, const int32_t *rows_dev, int64_t nrows, float cut, int32_t **pairs_dev,
+                          float **d_dev, int64_t *count) {
+    SearchBufs &S = SB(c);
+    S.res_n = 0;
+    *count = 0;
+    const int64_t N = c->N;
+    const int64_t nch = (N + 511) / 512;
+    const int64_t B = std::max<int64_t>(1, std::min<int64_t>(nrows, ((int64_t)1 << 28) / N));
+    GROW(S.seg_node, sizeof(int32_t) * B * nch);
+    GROW(S.seg_start, sizeof(int64_t) * B * nch);
+    GROW(S.seg_count, sizeof(int32_t) * B * nch);
+    GROW(S.seg_vbase, sizeof(int32_t) * B * nch);
+    GROW(S.ex_d, sizeof(float) * B * N);
+    int64_t rcap = std::max<int64_t>((int64_t)S.res_d.bytes / sizeof(float), 1 << 16);
+    GROW_KEEP(S.res_pairs, sizeof(int32_t) * 2 * rcap, 0);
+    GROW_KEEP(S.res_d, sizeof(float) * rcap, 0);
+    for (int64_t r0 = 0; r0 < nrows; r0 += B) {
+        const int64_t nb = std::min(B, nrows - r0);
+        k_row_segments<<<nblk(nb * nch), 256, 0, c->stream>>>(nb, N, nch, rows_dev + r0, (int32_t *)S.seg_node.p,
+                                                              (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p,
+                                                              (int32_t *)S.seg_vbase.p); note_launch();
+        CKS(cudaGetLastError());
+        recon_status st = score_segments_device(c, (int32_t *)S.seg_node.p, (int64_t *)S.seg_start.p,
+                                                (int32_t *)S.seg_count.p, (int32_t *)S.seg_vbase.p, nb * nch,
+                                                nullptr, nb * N, nullptr, (float *)S.ex_d.p);
+        if (st != RECON_OK) return st;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH3), 0, sizeof(unsigned long long), c->stream));
+            k_row_select<<<nblk(nb * N), 256, 0, c->stream>>>(nb, N, rows_dev + r0, (float *)S.ex_d.p, cut,
+                                                               (int32_t *)S.res_pairs.p + 2 * S.res_n,
+                                                               (float *)S.res_d.p + S.res_n, rcap - S.res_n,
+                                                               counter(c, CNT_SCRATCH3)); note_launch();
+            CKS(cudaGetLastError());
+            unsigned long long got = 0;
+            st = read_counter(c, CNT_SCRATCH3, &got);
+            if (st != RECON_OK) return st;
+            if (S.res_n + (int64_t)got <= rcap) {
+                S.res_n += (int64_t)got;
+                break;
+            }
+            // the output did not fit: grow it (keeping what is there) and select again
+            rcap = S.res_n + (int64_t)got + (int64_t)got / 4 + 1024;
+            GROW_KEEP(S.res_pairs, sizeof(int32_t) * 2 * rcap, sizeof(int32_t) * 2 * S.res_n);
+            GROW_KEEP(S.res_d, sizeof(float) * rcap, sizeof(float) * S.res_n);
+        }
+    }
+    recon_status st = check_err_flags(c, "row scoring");
+    if (st != RECON_OK) return st;
+    st = finish_results(c, std::max<int64_t>(S.res_n, 1), count);
     if (st != RECON_OK) return st;
     *pairs_dev = (int32_t *)S.out_pairs.p;
     *d_dev = (float *)S.out_d.p;

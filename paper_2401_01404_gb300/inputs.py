@@ -206,6 +206,11 @@ class Workload:
     k: int = 16
     kappa: float = 1.0
     extra: dict = field(default_factory=dict)
+    lam: float = 0.0          # the penalty this workload is run with
+
+    def __post_init__(self):
+        if not self.lam:
+            self.lam = default_lambda(self.N, self.M)
 
     def samples_major(self) -> np.ndarray:
         """The samples as the public API takes them: sample-major M x N."""
@@ -244,6 +249,11 @@ def config(name: str, device: str = "cpu", sweeps: int | None = None, M: int | N
                         diagonal 1.0 + sum|off| = 1.8; per-node k drawn from 8..64.
     ising_n1e6_m200   : N=1000000, M=200, Erdos-Renyi mean degree 5, w ~ N(0, 0.3^2), h = 0;
                         k=16, kappa=1.
+    Penalty: lambda = c sqrt(2 M ln N) with c = 1, except c = 2 for the two large
+    Ising workloads: there c = 1 would leave about 1% of all N^2/2 pairs (pure
+    sampling noise, |g| above lambda) with a nonzero optimum, while c = 2 keeps
+    that number O(N) (the union bound over the pairs), the sparsity the penalty is
+    there for.
     Optional overrides shrink a workload for tests (N, M, sweeps)."""
     if name == "ising_n100_m200":
         return ising_workload(name, N or 100, M or 200, "er", 3, "normal", 0.5, 0.1,
@@ -252,11 +262,15 @@ def config(name: str, device: str = "cpu", sweeps: int | None = None, M: int | N
         return ising_workload(name, N or 2000, M or 1000, "regular", 4, "pm", 0.3, 0.0,
                               sweeps or 1000, 2000, 16, 2.0, device)
     if name == "ising_n1e5_m500":
-        return ising_workload(name, N or 100000, M or 500, "er", 5, "normal", 0.3, 0.0,
-                              sweeps or 1000, 3000, 16, 1.0, device)
+        wl = ising_workload(name, N or 100000, M or 500, "er", 5, "normal", 0.3, 0.0,
+                            sweeps or 1000, 3000, 16, 1.0, device)
+        wl.lam = default_lambda(wl.N, wl.M, 2.0)
+        return wl
     if name == "ising_n1e6_m200":
-        return ising_workload(name, N or 1000000, M or 200, "er", 5, "normal", 0.3, 0.0,
-                              sweeps or 1000, 5000, 16, 1.0, device)
+        wl = ising_workload(name, N or 1000000, M or 200, "er", 5, "normal", 0.3, 0.0,
+                            sweeps or 1000, 5000, 16, 1.0, device)
+        wl.lam = default_lambda(wl.N, wl.M, 2.0)
+        return wl
     if name == "gauss_n20000_m2000":
         L1, L2 = (100, 200) if N is None else (int(math.isqrt(N // 2)), N // int(math.isqrt(N // 2)))
         MM = M or 2000

@@ -75,6 +75,8 @@ _EXPORTS = {
     "recon_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "recon_load": (C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p]),
     "recon_set_list_lengths": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "recon_row_best": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_float, C.c_void_p, C.c_void_p, C.c_int64,
+                                 C.c_void_p]),
     "recon_knn_graph": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "recon_proposal_param_count": (C.c_int64, []),
     "recon_default_train_opts": (None, [C.c_void_p]),
@@ -274,6 +276,22 @@ def recon_set_list_lengths(ctx, k=None):
     _check(lib().recon_set_list_lengths(ctx, a.ctypes.data, len(a)), ctx)
 
 
+def recon_row_best(ctx, rows, d_cut: float, cap: int = None):
+    """All pairs incident to `rows` with d < d_cut, exact, ascending (d, i, j):
+    (pairs [n x 2], d [n], count found)."""
+    r = np.ascontiguousarray(np.asarray(rows, dtype=np.int32).ravel())
+    n = C.c_int64(0)
+    if cap is None:
+        _check(lib().recon_row_best(ctx, r.ctypes.data, len(r), C.c_float(d_cut), None, None, 0, C.byref(n)), ctx)
+        cap = n.value
+    p = np.empty((max(cap, 1), 2), dtype=np.int32)
+    d = np.empty(max(cap, 1), dtype=np.float32)
+    _check(lib().recon_row_best(ctx, r.ctypes.data, len(r), C.c_float(d_cut), p.ctypes.data, d.ctypes.data, cap,
+                                C.byref(n)), ctx)
+    k = min(n.value, cap)
+    return p[:k], d[:k], n.value
+
+
 def recon_knn_graph(ctx):
     """The first-level k-NN lists of the last FindBest search: (ids [N x k],
     d [N x k]), padding id -1 / d +inf; empty arrays when no lists were built."""
@@ -384,6 +402,9 @@ class Recon:
 
     def best_pairs(self, k: int, kappa: float):
         return recon_best_pairs(self.ctx, k, kappa, self.N)
+
+    def row_best(self, rows, d_cut: float, cap: int = None):
+        return recon_row_best(self.ctx, rows, d_cut, cap)
 
     def knn_graph(self):
         return recon_knn_graph(self.ctx)

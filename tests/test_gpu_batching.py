@@ -38,7 +38,7 @@ def c4():
 def test_uneven_lists_on_the_lattice(R, oracle, c4):
     wl = c4
     Xs = np.ascontiguousarray(wl.X.T.astype(np.float32))
-    lam = inputs.default_lambda(wl.N, wl.M)
+    lam = wl.lam
     nnd = R.Recon(Xs, R.RECON_GAUSSIAN, lam=lam, timing=1)
     kk = wl.extra["k_per_node"]
     assert kk.min() >= 8 and kk.max() <= 64

@@ -38,7 +38,7 @@ def c3():
 
 def test_precision_workload_sampled_pairs_and_rows(R, oracle, c3):
     wl = c3
-    lam = inputs.default_lambda(wl.N, wl.M)
+    lam = wl.lam
     scr = R.Recon(wl.samples_major(), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
     p, d = scr.best_pairs(16, 1.0)
     assert len(p) == wl.N and np.all(np.diff(d) >= 0)
