@@ -18,8 +18,8 @@
 // the paper's own suggestion (App. B, "Gradient as distance").
 //
 // Kernel layout: a persistent grid; each CTA walks the upper-triangular 128x128
-// tiles of G.  Warp 4 issues TMA loads of 128x64 bf16 tiles (128-byte swizzle)
-// into a 4-stage ring, warp 5 issues tcgen05.mma (M=128, N=128, K=16) into one
+// tiles of G (in bands of 16 tile rows, for L2 reuse).  Warp 4 issues TMA loads of 128x64 bf16 tiles (128-byte swizzle)
+// into a 6-stage ring, warp 5 issues tcgen05.mma (M=128, N=128, K=16) into one
 // of two TMEM accumulators of 128 columns, warps 0-3 drain the other
 // accumulator (tcgen05.ld, one TMEM lane = one row per thread) and append the
 // surviving pairs.  Every wait is bounded (1 s); on a timeout the kernel sets
@@ -34,7 +34,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
 constexpr uint32_t TMEM_COLS = 256;  // two accumulators of 128 f32 columns
 constexpr int THREADS = 192;
@@ -63,17 +63,25 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t par) {
         : "memory");
     return ok != 0;
 }
-// bounded wait (1 s of wall time); false on timeout or when another role gave up
+// bounded wait (about 1 s of wall time); false on timeout or when another role
+// gave up.  The global timer is a slow special-register read, so it is read only
+// every 256 failed polls (a completed barrier costs one try_wait and no read).
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile int *abort) {
-    const uint64_t t0 = gtimer();
-    while (!mbar_try(b, par)) {
-        if (*abort) return false;
-        if (gtimer() - t0 > 1000000000ull) {
-            *abort = 1;
-            return false;
+    if (mbar_try(b, par)) return true;
+    uint64_t t0 = 0;
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try(b, par)) return true;
+        if ((n & 255u) == 0) {
+            if (*abort) return false;
+            const uint64_t now = gtimer();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > 1000000000ull) {
+                *abort = 1;
+                return false;
+            }
         }
     }
-    return true;
 }
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
     asm volatile(
@@ -109,18 +117,41 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])   \
         : "r"(taddr))
 
-// tile t of the upper triangle (row-major, bi <= bj) of a T x T tile grid
+// Tile order over the upper triangle (bi <= bj) of a T x T tile grid: bands of
+// GROUP tile rows, each band walked column by column (in a column, its rows in
+// order).  The tiles that the persistent CTAs hold at one time then form a
+// compact block of about GROUP rows x (grid / GROUP) columns: the band's A tiles
+// stay in L2 for the whole band, and each B tile is read from memory once per
+// band instead of once per tile row.
+constexpr int GROUP = 16;
+__device__ __forceinline__ int64_t band_start(int64_t g, int64_t T) {
+    // tiles before band g; every band before it is full
+    return g * GROUP * (GROUP + 1) / 2 + (int64_t)GROUP * (g * T - (int64_t)GROUP * g * (g + 1) / 2);
+}
 __device__ __forceinline__ void tile_of(int64_t t, int T, int &bi, int &bj) {
-    double TT = (double)T;
-    double disc = (2 * TT + 1) * (2 * TT + 1) - 8.0 * (double)t;
-    int64_t r = (int64_t)floor(((2 * TT + 1) - sqrt(fmax(disc, 0.0))) / 2);
-    auto start = [&](int64_t q) { return q * (2 * (int64_t)T - q + 1) / 2; };
-    if (r < 0) r = 0;
-    if (r > T - 1) r = T - 1;
-    while (r > 0 && start(r) > t) --r;
-    while (r < T - 1 && start(r + 1) <= t) ++r;
-    bi = (int)r;
-    bj = (int)(t - start(r) + r);
+    const int64_t nb = ((int64_t)T + GROUP - 1) / GROUP;
+    int64_t lo = 0, hi = nb - 1;
+    while (lo < hi) {  // the last band that starts at or before t
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (band_start(mid, T) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t r0 = lo * GROUP;
+    const int64_t Gb = min((int64_t)GROUP, (int64_t)T - r0);
+    int64_t u = t - band_start(lo, T);
+    const int64_t tri = Gb * (Gb + 1) / 2;
+    if (u < tri) {  // the band's own triangle: column c holds rows r0 .. r0 + c
+        int64_t c = 0;
+        while ((c + 1) * (c + 2) / 2 <= u) ++c;
+        bi = (int)(r0 + u - c * (c + 1) / 2);
+        bj = (int)(r0 + c);
+        return;
+    }
+    u -= tri;
+    bi = (int)(r0 + u % Gb);
+    bj = (int)(r0 + Gb + u / Gb);
 }
 
 struct ScreenArgs {
@@ -227,49 +258,82 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             }
         }
     } else {  // epilogue warps 0-3: row 32*warp + lane of each tile
+        // per-warp copy of the tile's column norms (the margin's l_j), read as
+        // 128-bit broadcasts
+        float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * BN;
         int64_t it = 0;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
             const int b = (int)(it & 1);
-            if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
-            tc_fence_after();
             int bi, bj;
             tile_of(t, a.T, bi, bj);
             const int i = bi * BM + 32 * warp + lane;
+            const int jt = bj * BN;
+            // keep iff |g| > lambda - margin, written |g| + s c_j > thr:
+            //   sum margin     rel (l_i + l_j):  c_j = rel l_j, s = 1,        thr = lambda - rel l_i
+            //   product margin rel l_i l_j:      c_j = l_j,     s = rel l_i,  thr = lambda
             const float li = (a.l1 && i < a.n) ? a.l1[i] : 0.f;
-            // two passes over the accumulator: count this warp's survivors, reserve
-            // their slots with one atomic, then write them
-            unsigned long long base = 0, taken = 0;
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int c = 0; c < BN / 32; ++c) {
-                    uint32_t r[32];
-                    TMEM_LD32(r, tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN + 32 * c));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    const int j0 = bj * BN + 32 * c;
-                    const float lj_lane = (a.l1 && (j0 + lane) < a.n) ? a.l1[j0 + lane] : 0.f;
+            const float sc = a.product_margin ? a.rel_err * li : 1.f;
+            const float thr = a.product_margin ? a.lambda : a.lambda - a.rel_err * li;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int j = j0 + q;
-                        const float lj = __shfl_sync(0xffffffffu, lj_lane, q);
-                        const float g = __uint_as_float(r[q]);
-                        const float margin = a.rel_err * (a.product_margin ? li * lj : li + lj);
-                        bool keep = i < j && j < a.n && fabsf(g) > a.lambda - margin;
-                        if (keep && a.skip_stored) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
-                        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                        if (pass == 1 && keep) {
-                            const int64_t pos = (int64_t)(base + taken) + __popc(bal & ((1u << lane) - 1u));
-                            if (pos < a.cap) {
-                                a.out[2 * pos] = i;
-                                a.out[2 * pos + 1] = j;
-                            }
-                        }
-                        taken += (unsigned long long)__popc(bal);
-                    }
+            for (int u = 0; u < 4; ++u) {
+                const int j = jt + 4 * lane + u;
+                const float lj = (a.l1 && j < a.n) ? a.l1[j] : 0.f;
+                cn[4 * lane + u] = a.product_margin ? lj : a.rel_err * lj;
+            }
+            __syncwarp();
+            if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN);
+            // fast path: all 128 columns at once, one wait, no shuffles or votes
+            bool any = false;
+            {
+                uint32_t r[BN];
+                TMEM_LD32(r, taddr);
+                TMEM_LD32((r + 32), taddr + 32);
+                TMEM_LD32((r + 64), taddr + 64);
+                TMEM_LD32((r + 96), taddr + 96);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q4 = 0; q4 < BN / 4; ++q4) {
+                    const float4 c4 = ((const float4 *)cn)[q4];
+                    any |= fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr;
+                    any |= fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr;
+                    any |= fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr;
+                    any |= fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr;
                 }
-                if (pass == 0) {
-                    if (taken == 0) break;
-                    if (lane == 0) base = atomicAdd(a.count, taken);
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    taken = 0;
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                // rare path (diagonal tiles, tiles holding a survivor): count this
+                // warp's survivors, reserve their slots with one atomic, write them
+                unsigned long long base = 0, taken = 0;
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int c = 0; c < BN / 32; ++c) {
+                        uint32_t r[32];
+                        TMEM_LD32(r, taddr + (uint32_t)(32 * c));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int j = jt + 32 * c + q;
+                            const float g = __uint_as_float(r[q]);
+                            bool keep = i < j && j < a.n && fabsf(g) + sc * cn[32 * c + q] > thr;
+                            if (keep && a.skip_stored) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
+                            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                            if (pass == 1 && keep) {
+                                const int64_t pos = (int64_t)(base + taken) + __popc(bal & ((1u << lane) - 1u));
+                                if (pos < a.cap) {
+                                    a.out[2 * pos] = i;
+                                    a.out[2 * pos + 1] = j;
+                                }
+                            }
+                            taken += (unsigned long long)__popc(bal);
+                        }
+                    }
+                    if (pass == 0) {
+                        if (taken == 0) break;
+                        if (lane == 0) base = atomicAdd(a.count, taken);
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        taken = 0;
+                    }
                 }
             }
             tc_fence_before();
@@ -383,7 +447,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256;
+    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + 4 * BN * sizeof(float);
     static int attr_device = -1;  // the attribute is per device; set it once for each
     if (attr_device != c->device) {
         cudaError_t e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
