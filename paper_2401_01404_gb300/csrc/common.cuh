@@ -337,12 +337,12 @@ cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned lo
 cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1);
 float screen_rel_err(int model, int Mp);
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
-                          unsigned long long *count, float margin_scale, int *tiles_out);
+                          unsigned long long *count, float margin_scale, double *flop_out);
 // general form: operands of K columns (a multiple of 64), threshold `thr` on |G_ij|,
 // margin rel * (l_i + l_j) (or l_i l_j) when l1 is given, stored couplings skipped when skip_stored
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
-                             unsigned long long *count, int *tiles_out);
+                             unsigned long long *count, double *flop_out);
 
 // host helpers (api.cu)
 recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...);

@@ -17,10 +17,12 @@
 // Algorithm 3 over the whole node set).  The gradient as a cheap proxy for d is
 // the paper's own suggestion (App. B, "Gradient as distance").
 //
-// Kernel layout: a persistent grid; each CTA walks the upper-triangular 128x128
-// tiles of G (in bands of 16 tile rows, for L2 reuse).  Warp 4 issues TMA loads of 128x64 bf16 tiles (128-byte swizzle)
-// into a 6-stage ring, warp 5 issues tcgen05.mma (M=128, N=128, K=16) into one
-// of two TMEM accumulators of 128 columns, warps 0-3 drain the other
+// Kernel layout: a persistent grid; each CTA walks 128x256 units of G: the two
+// row halves of each 256x256 super-tile of the upper triangle (super-tiles in
+// bands of 8 super-rows, for L2 reuse).  Warp 4 issues TMA loads of 128x64 (A)
+// and 256x64 (B) bf16 tiles (128-byte swizzle) into a 4-stage ring, warp 5
+// issues tcgen05.mma (M=128, N=256, K=16) into one of two TMEM accumulators of
+// 256 columns, warps 0-3 drain the other
 // accumulator (tcgen05.ld, one TMEM lane = one row per thread) and append the
 // surviving pairs.  Every wait is bounded (1 s); on a timeout the kernel sets
 // an error word, lets its own copies land, frees TMEM and returns.
@@ -34,9 +36,12 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
+// a unit of work is a 128 x 256 block of G: rows BM from A, columns BN from B;
+// units are the two 128-row halves of the 256 x 256 super-tiles (SUP) of the
+// upper triangle
+constexpr int BM = 128, BN = 256, SUP = 256, BK = 64, STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-constexpr uint32_t TMEM_COLS = 256;  // two accumulators of 128 f32 columns
+constexpr uint32_t TMEM_COLS = 512;  // two accumulators of 256 f32 columns
 constexpr int THREADS = 192;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -123,7 +128,7 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 // compact block of about GROUP rows x (grid / GROUP) columns: the band's A tiles
 // stay in L2 for the whole band, and each B tile is read from memory once per
 // band instead of once per tile row.
-constexpr int GROUP = 16;
+constexpr int GROUP = 8;
 __device__ __forceinline__ int64_t band_start(int64_t g, int64_t T) {
     // tiles before band g; every band before it is full
     return g * GROUP * (GROUP + 1) / 2 + (int64_t)GROUP * (g * T - (int64_t)GROUP * g * (g + 1) / 2);
@@ -154,10 +159,58 @@ __device__ __forceinline__ void tile_of(int64_t t, int T, int &bi, int &bj) {
     bj = (int)(r0 + Gb + u / Gb);
 }
 
+// Unit u is half u & 1 of super-tile u >> 1.  Each role of a CTA visits its
+// units in increasing order, so the band only moves forward: the walker keeps
+// the current band and its start, and maps a unit with 32-bit arithmetic
+// (tile_of above is the same order in closed form).
+struct UnitWalker {
+    int T;
+    int64_t nb, g = -1, g_start = 0, g_next = 0;
+    __device__ explicit UnitWalker(int T_) : T(T_), nb(((int64_t)T_ + GROUP - 1) / GROUP) {}
+    // first row of A and of B of unit u
+    __device__ __forceinline__ void map(int64_t u, int &ra, int &rb) {
+        const int64_t st = u >> 1;
+        if (g < 0) {
+            int bi, bj;
+            tile_of(st, T, bi, bj);
+            g = bi / GROUP;
+            g_start = band_start(g, T);
+            g_next = g + 1 < nb ? band_start(g + 1, T) : INT64_MAX;
+        }
+        while (st >= g_next) {
+            ++g;
+            g_start = g_next;
+            g_next = g + 1 < nb ? band_start(g + 1, T) : INT64_MAX;
+        }
+        const int r0 = (int)(g * GROUP);
+        const int Gb = min(GROUP, T - r0);
+        uint32_t v = (uint32_t)(st - g_start);
+        const uint32_t tri = (uint32_t)(Gb * (Gb + 1) / 2);
+        int bi, bj;
+        if (v < tri) {
+            uint32_t c = 0;
+            while ((c + 1) * (c + 2) / 2 <= v) ++c;
+            bi = r0 + (int)(v - c * (c + 1) / 2);
+            bj = r0 + (int)c;
+        } else {
+            v -= tri;
+            if (Gb == GROUP) {
+                bi = r0 + (int)(v % GROUP);
+                bj = r0 + Gb + (int)(v / GROUP);
+            } else {
+                bi = r0 + (int)(v % (uint32_t)Gb);
+                bj = r0 + Gb + (int)(v / (uint32_t)Gb);
+            }
+        }
+        ra = bi * SUP + (int)(u & 1) * BM;
+        rb = bj * SUP;
+    }
+};
+
 struct ScreenArgs {
     int n;              // nodes
-    int T;              // tiles per side
-    int64_t ntiles;     // T (T + 1) / 2
+    int T;              // super-tiles per side
+    int64_t ntiles;     // units: 2 T (T + 1) / 2
     int nk;             // K / BK
     float lambda;
     float rel_err;      // margin per unit of the per-node norms
@@ -208,16 +261,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
 
     if (warp == 4) {
         if (lane == 0) {  // TMA producer
+            UnitWalker walk(a.T);
             int64_t kb_all = 0;
             for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x) {
-                int bi, bj;
-                tile_of(t, a.T, bi, bj);
+                int ra, rb;
+                walk.map(t, ra, rb);
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
                     const int s = (int)(kb_all % STAGES);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
                     mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-                    tma_2d(sA + s * A_BYTES, &tA, kb * BK, bi * BM, full + s);
-                    tma_2d(sB + s * B_BYTES, &tB, kb * BK, bj * BN, full + s);
+                    tma_2d(sA + s * A_BYTES, &tA, kb * BK, ra, full + s);
+                    tma_2d(sB + s * B_BYTES, &tB, kb * BK, rb, full + s);
                 }
             }
             // let every copy issued above land before the CTA can leave
@@ -261,78 +315,133 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         // per-warp copy of the tile's column norms (the margin's l_j), read as
         // 128-bit broadcasts
         float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * BN;
+        UnitWalker walk(a.T);
+        // the column norms l_j of a unit: lane holds columns 8 lane .. 8 lane + 7,
+        // loaded one unit ahead so that their latency hides behind the compare
+        auto load_norms = [&](int jt, float4 &n0, float4 &n1) {
+            const int j = jt + 8 * lane;
+            if (a.l1 && j + 7 < a.n) {
+                n0 = *(const float4 *)(a.l1 + j);
+                n1 = *(const float4 *)(a.l1 + j + 4);
+            } else {
+                float q[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) q[u] = (a.l1 && j + u < a.n) ? a.l1[j + u] : 0.f;
+                n0 = make_float4(q[0], q[1], q[2], q[3]);
+                n1 = make_float4(q[4], q[5], q[6], q[7]);
+            }
+        };
+        auto load_row = [&](int ra_) {
+            const int i_ = ra_ + 32 * warp + lane;
+            return (a.l1 && i_ < a.n) ? a.l1[i_] : 0.f;
+        };
+        int ra = 0, jt = 0;
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        float li_n = 0.f;
+        if ((int64_t)blockIdx.x < a.ntiles) {
+            walk.map(blockIdx.x, ra, jt);
+            load_norms(jt, n0, n1);
+            li_n = load_row(ra);
+        }
         int64_t it = 0;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
             const int b = (int)(it & 1);
-            int bi, bj;
-            tile_of(t, a.T, bi, bj);
-            const int i = bi * BM + 32 * warp + lane;
-            const int jt = bj * BN;
+            const int i = ra + 32 * warp + lane;
+            const int jt_cur = jt;
             // keep iff |g| > lambda - margin, written |g| + s c_j > thr:
             //   sum margin     rel (l_i + l_j):  c_j = rel l_j, s = 1,        thr = lambda - rel l_i
             //   product margin rel l_i l_j:      c_j = l_j,     s = rel l_i,  thr = lambda
-            const float li = (a.l1 && i < a.n) ? a.l1[i] : 0.f;
+            const float li = li_n;
             const float sc = a.product_margin ? a.rel_err * li : 1.f;
             const float thr = a.product_margin ? a.lambda : a.lambda - a.rel_err * li;
+            const float f = a.product_margin ? 1.f : a.rel_err;
+            const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
+            const float4 c1 = make_float4(f * n1.x, f * n1.y, f * n1.z, f * n1.w);
+            ((float4 *)cn)[2 * lane] = c0;
+            ((float4 *)cn)[2 * lane + 1] = c1;
+            float cmax = fmaxf(fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w)), fmaxf(fmaxf(c1.x, c1.y), fmaxf(c1.z, c1.w)));
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = jt + 4 * lane + u;
-                const float lj = (a.l1 && j < a.n) ? a.l1[j] : 0.f;
-                cn[4 * lane + u] = a.product_margin ? lj : a.rel_err * lj;
+            for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            // the next unit's mapping and norms, in flight during this unit's compare
+            if (t + gridDim.x < a.ntiles) {
+                walk.map(t + gridDim.x, ra, jt);
+                load_norms(jt, n0, n1);
+                li_n = load_row(ra);
             }
             __syncwarp();
             if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN);
-            // fast path: all 128 columns at once, one wait, no shuffles or votes
+            // fast path, 64 columns at a time: max |g| against the loosest
+            // threshold of the unit (thr - s max c_j); the exact per-column test
+            // only when that fires
             bool any = false;
-            {
-                uint32_t r[BN];
-                TMEM_LD32(r, taddr);
-                TMEM_LD32((r + 32), taddr + 32);
-                TMEM_LD32((r + 64), taddr + 64);
-                TMEM_LD32((r + 96), taddr + 96);
+#pragma unroll 1
+            for (int hf = 0; hf < BN / 64; ++hf) {
+                uint32_t r[64];
+                const uint32_t ta = taddr + (uint32_t)(64 * hf);
+                TMEM_LD32(r, ta);
+                TMEM_LD32((r + 32), ta + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float m = 0.f;
 #pragma unroll
-                for (int q4 = 0; q4 < BN / 4; ++q4) {
-                    const float4 c4 = ((const float4 *)cn)[q4];
-                    any |= fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr;
-                    any |= fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr;
-                    any |= fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr;
-                    any |= fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr;
+                for (int q = 0; q < 64; ++q) m = fmaxf(m, fabsf(__uint_as_float(r[q])));
+                if (m + sc * cmax > thr) {
+                    const float4 *c4p = (const float4 *)(cn + 64 * hf);
+#pragma unroll
+                    for (int q4 = 0; q4 < 16; ++q4) {
+                        const float4 c4 = c4p[q4];
+                        any |= fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr;
+                        any |= fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr;
+                        any |= fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr;
+                        any |= fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr;
+                    }
                 }
             }
             if (__any_sync(0xffffffffu, any)) {
-                // rare path (diagonal tiles, tiles holding a survivor): count this
-                // warp's survivors, reserve their slots with one atomic, write them
-                unsigned long long base = 0, taken = 0;
+                // rare path (diagonal units, units holding a survivor): each thread
+                // counts its row's survivors, one scan and one atomic reserve the
+                // warp's slots, then each thread writes its own
+                int mine = 0;
+                unsigned long long base = 0;
                 for (int pass = 0; pass < 2; ++pass) {
+                    int w = 0;
                     for (int c = 0; c < BN / 32; ++c) {
                         uint32_t r[32];
                         TMEM_LD32(r, taddr + (uint32_t)(32 * c));
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
-                            const int j = jt + 32 * c + q;
-                            const float g = __uint_as_float(r[q]);
-                            bool keep = i < j && j < a.n && fabsf(g) + sc * cn[32 * c + q] > thr;
+                            const int j = jt_cur + 32 * c + q;
+                            bool keep = i < j && j < a.n &&
+                                        fabsf(__uint_as_float(r[q])) + sc * cn[32 * c + q] > thr;
                             if (keep && a.skip_stored) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
-                            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                            if (pass == 1 && keep) {
-                                const int64_t pos = (int64_t)(base + taken) + __popc(bal & ((1u << lane) - 1u));
-                                if (pos < a.cap) {
-                                    a.out[2 * pos] = i;
-                                    a.out[2 * pos + 1] = j;
+                            if (keep) {
+                                if (pass == 1) {
+                                    const int64_t pos = (int64_t)base + w;
+                                    if (pos < a.cap) {
+                                        a.out[2 * pos] = i;
+                                        a.out[2 * pos + 1] = j;
+                                    }
                                 }
+                                ++w;
                             }
-                            taken += (unsigned long long)__popc(bal);
                         }
                     }
                     if (pass == 0) {
-                        if (taken == 0) break;
-                        if (lane == 0) base = atomicAdd(a.count, taken);
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        taken = 0;
+                        mine = w;
+                        int incl = w;  // inclusive scan over the warp
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const int total = __shfl_sync(0xffffffffu, incl, 31);
+                        if (total == 0) break;
+                        unsigned long long wb = 0;
+                        if (lane == 31) wb = atomicAdd(a.count, (unsigned long long)total);
+                        wb = __shfl_sync(0xffffffffu, wb, 31);
+                        base = wb + (unsigned long long)(incl - mine);
                     }
                 }
             }
@@ -427,7 +536,7 @@ float screen_rel_err(int model, int Mp) {
 
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
-                             unsigned long long *count, int *tiles_out) {
+                             unsigned long long *count, double *flop_out) {
     if (K % BK) return cudaErrorInvalidValue;
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
@@ -438,12 +547,12 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     CUtensorMap ta, tb;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
     cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t box_a[2] = {BK, BM}, box_b[2] = {BK, BN};
     cuuint32_t es[2] = {1, 1};
-    if (g_encode(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(A), dims, strides, box, es,
+    if (g_encode(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(A), dims, strides, box_a, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        g_encode(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), dims, strides, box, es,
+        g_encode(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), dims, strides, box_b, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -456,8 +565,8 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     }
     ScreenArgs a;
     a.n = (int)c->N;
-    a.T = (int)((c->N + BM - 1) / BM);
-    a.ntiles = (int64_t)a.T * (a.T + 1) / 2;
+    a.T = (int)((c->N + SUP - 1) / SUP);
+    a.ntiles = (int64_t)a.T * (a.T + 1);  // two units per super-tile
     a.nk = K / BK;
     a.lambda = thr;
     a.rel_err = rel;
@@ -472,12 +581,12 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);
     k_screen<<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();
-    if (tiles_out) *tiles_out = (int)std::min<int64_t>(a.ntiles, 0x7fffffff);
+    if (flop_out) *flop_out = 2.0 * BM * BN * (double)K * (double)a.ntiles;
     return cudaGetLastError();
 }
 
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
-                          unsigned long long *count, float margin_scale, int *tiles_out) {
+                          unsigned long long *count, float margin_scale, double *flop_out) {
     return launch_screen_ex(c, A, B, 2 * (int)c->Mp, (float)c->opt.lambda, l1, margin_scale,
-                            c->model == RECON_GAUSSIAN, true, out, cap, count, tiles_out);
+                            c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out);
 }

@@ -1433,13 +1433,13 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
             }
             CKS(cudaEventRecord(ea, c->stream));
         }
-        int tiles = 0;
+        double flop = 0.0;
         CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
-                          counter(c, CNT_SCRATCH1), rel, &tiles));
+                          counter(c, CNT_SCRATCH1), rel, &flop));
         if (c->opt.timing) {
             CKS(cudaEventRecord(eb, c->stream));
             c->timed.push_back({ea, eb, -1});
-            c->stats.screen_flop += 2.0 * 128.0 * 128.0 * (double)K * (double)tiles;
+            c->stats.screen_flop += flop;
         }
         recon_status st = read_counter(c, CNT_SCRATCH1, &nsurv);
         if (st != RECON_OK) return st;
