@@ -49,6 +49,8 @@ def _args():
                     help="also measure time to 0.99 recall on this large workload (subsample ground truth)")
     ap.add_argument("--scale-rows", type=int, default=10000)
     ap.add_argument("--scale-caps", type=int, default=8)
+    ap.add_argument("--screen-bench", type=int, nargs=2, metavar=("N", "M"), default=None,
+                    help="time only the tensor-core screen on N nodes x M seeded random spins")
     return ap.parse_args()
 
 
@@ -400,11 +402,7 @@ def run_ours(a):
         if world > 1:
             dist.destroy_process_group()
         return
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    peaks = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     avg_launch_s = score_ms / 1e3 / max(score_launches, 1)
     bytes_per_launch = BYTES_PER_PAIR_SAMPLE * wl.M * score_pairs / max(score_launches, 1)
@@ -432,7 +430,7 @@ def run_ours(a):
                 "what": "recon_init from pinned host samples + one GCD step + model to host, per step"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "k_score (exact pair gain)", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": _score_traffic(wl.name),
                      "bytes_per_pair_sample": BYTES_PER_PAIR_SAMPLE,
                      "avg_launch_ms": avg_launch_s * 1e3, "launches": int(score_launches),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
@@ -493,8 +491,72 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per launch of the segmented pair scorer on the
+# 2000-node workload, the mean over the 47 launches of one ncu capture of
+# `python bench.py --steps 2 --warmup 1 --no-cpu --no-recall` (summarised under
+# profiles/); it describes the scorer source it was taken on and is reported as
+# null once that source changes
+SCORE_TRAFFIC = {"workload": "ising_n2000_m1000", "bytes_per_launch": 9045673,
+                 "source": "paper_2401_01404_gb300/csrc/ising.cu", "sha256": "0e76ea3f31a39fa31b73309106bfa0cbb0a08a3dd92d66151fa8cb546bf55e85"}
+
+
+def _score_traffic(workload):
+    import hashlib
+
+    if workload != SCORE_TRAFFIC["workload"]:
+        return None
+    try:
+        cur = hashlib.sha256(open(os.path.join(ROOT, SCORE_TRAFFIC["source"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return SCORE_TRAFFIC["bytes_per_launch"] if cur == SCORE_TRAFFIC["sha256"] else None
+
+
+def _peaks():
+    """The measured peaks of this GPU pool (HBM copy GB/s, bf16 TFLOP/s)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def run_screen_bench(a):
+    """The screen alone (the dominant kernel of the exact best-pairs path) on
+    seeded uniform random spins, lambda = 2 sqrt(2 M ln N): one JSON line with
+    the per-launch time and its fraction of the measured bf16 peak."""
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import inputs, recon as R
+
+    N, M = a.screen_bench
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(int(inputs.rng(N + M, inputs.SAMPLES).integers(1 << 62)))
+    X = (torch.randint(0, 2, (M, N), generator=gen, device="cuda", dtype=torch.int8) * 2 - 1).contiguous()
+    ctx = R.Recon(X, R.RECON_ISING, lam=inputs.default_lambda(N, M, 2.0), knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    for _ in range(max(a.warmup, 1)):
+        ctx.best_pairs(16, 1.0)
+    s0 = ctx.stats()
+    for _ in range(a.steps):
+        ctx.best_pairs(16, 1.0)
+    torch.cuda.synchronize()
+    s1 = ctx.stats()
+    ms = (s1["screen_ms"] - s0["screen_ms"]) / a.steps
+    tf = (s1["screen_flop"] - s0["screen_flop"]) / a.steps / (ms / 1e3) / 1e12
+    peaks = _peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    print(json.dumps({"kernel": "k_screen", "N": N, "M": M, "steps": a.steps, "ms_per_launch": ms, "tflops": tf,
+                      "peak": bf16, "frac": tf / bf16,
+                      "survivors_per_launch": (s1["screen_survivors"] - s0["screen_survivors"]) / a.steps,
+                      "data": "seeded uniform random spins"}), flush=True)
+
+
 def main():
     a = _args()
+    if a.screen_bench:
+        run_screen_bench(a)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
