@@ -198,18 +198,18 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
     out["screen"] = {"tflops": st["screen_flop"] / (st["screen_ms"] / 1e3) / 1e12 if st["screen_ms"] else None,
                      "avg_launch_ms": st["screen_ms"] / max(st["screen_launches"], 1),
                      "survivors_per_call": st["screen_survivors"] / max(st["screen_launches"], 1)}
-    for kk, learned in ((k, False), (2 * k, False), (k, True)):
+    for kk, learned, dist in ((k, False, 0), (2 * k, False, 0), (k, True, 0), (k, False, 1)):
         curve = []
         t_hit = None
         mode = R.RECON_SEED_LEARNED if learned else R.RECON_SEED_RANDOM
         for cap in range(1, 13):
             ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                          seed_mode=mode)
+                          seed_mode=mode, distance=dist)
             if learned:
                 R.recon_proposal_weights(ctx.ctx, weights)
             ctx.best_pairs(kk, kappa)  # warm
             ctx2 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                           seed_mode=mode)
+                           seed_mode=mode, distance=dist)
             if learned:
                 R.recon_proposal_weights(ctx2.ctx, weights)
             t0.record(stream)
@@ -224,7 +224,7 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
             if rec >= 0.99 and t_hit is None:
                 t_hit = dt
                 break
-        tag = ("learned_fp32" if learned else "plain_fp32") + ("" if kk == k else f"_k{kk}")
+        tag = ("learned_fp32" if learned else "gradient_fp32" if dist else "plain_fp32") + ("" if kk == k else f"_k{kk}")
         out[tag + "_s"] = t_hit
         out[tag + "_curve"] = curve
     return out
@@ -296,11 +296,12 @@ def _scale_recall(R, name, stream, rows_n, max_cap):
     tr.close()
     out["pretrain"] = {"seconds": round(time.perf_counter() - t, 2), "N": 100000, "loss_first": float(losses[0]),
                        "loss_last": float(losses[-1])}
-    for tag, mode in (("plain_fp32", R.RECON_SEED_RANDOM), ("learned_fp32", R.RECON_SEED_LEARNED)):
+    for tag, mode, dist in (("plain_fp32", R.RECON_SEED_RANDOM, 0), ("learned_fp32", R.RECON_SEED_LEARNED, 0),
+                            ("gradient_fp32", R.RECON_SEED_RANDOM, 1)):
         curve, t_hit = [], None
         for cap in range(1, max_cap + 1):
             ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                          seed_mode=mode)
+                          seed_mode=mode, distance=dist)
             if mode == R.RECON_SEED_LEARNED:
                 R.recon_proposal_weights(ctx.ctx, weights)
             ctx.best_pairs(k, kappa)  # allocates the buffers

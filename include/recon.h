@@ -74,6 +74,17 @@ typedef enum {
     RECON_SEED_LEARNED = 2 /* lists seeded from the learned sketch embedding */
 } recon_seed_mode;
 
+/* The distance the search ranks pairs by (App. B, "Gradient as distance").
+ *   GAIN      d(i,j) = -(max_w pi(W_ij <- w) - pi(W)), the exact gain of Algorithm 2.
+ *   GRADIENT  d(i,j) = -|d log pi / d W_ij| at the current W: the smooth part's
+ *             derivative D at W_ij, and D - lambda sign(W_ij) for a stored coupling
+ *             (a central difference of the penalty at W_ij = 0 is zero).  One pass
+ *             over the samples, no 1-D solve; recon_score returns it (w_out = the
+ *             current coupling), and the coordinate updates still solve each pair
+ *             exactly.  Not with RECON_KNN_SCREEN (whose survivors are the pairs with
+ *             |D| > lambda only): recon_init returns RECON_EUNSUPPORTED. */
+typedef enum { RECON_DIST_GAIN = 0, RECON_DIST_GRADIENT = 1 } recon_distance;
+
 typedef struct {
     double lambda;        /* Laplace prior penalty (App. A), >= 0 */
     uint64_t seed;        /* seed of every random choice of the search */
@@ -91,7 +102,8 @@ typedef struct {
     float learned_frac;   /* RECON_SEED_LEARNED: share of each initial list taken from the
                              proposal's best seeds, in (0, 1]; the rest are random ids
                              (0 selects the default 0.5) */
-    int32_t reserved[5];  /* zero */
+    int32_t distance;     /* recon_distance: the d(i, j) that the search ranks pairs by */
+    int32_t reserved[4];  /* zero */
 } recon_options;
 
 typedef struct {

@@ -252,6 +252,10 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     if (model == RECON_ISING && o.w_clamp > 8.f)
         return set_err(nullptr, RECON_EINVAL, "w_clamp above 8 is not supported for the Ising model");
     if (o.knn_mode < 0 || o.knn_mode > 3) return set_err(nullptr, RECON_EINVAL, "unknown knn_mode");
+    if (o.distance != RECON_DIST_GAIN && o.distance != RECON_DIST_GRADIENT)
+        return set_err(nullptr, RECON_EINVAL, "unknown distance");
+    if (o.distance == RECON_DIST_GRADIENT && o.knn_mode == RECON_KNN_SCREEN)
+        return set_err(nullptr, RECON_EUNSUPPORTED, "the gradient distance ranks pairs the screen does not keep");
     if (!(o.learned_frac >= 0.f && o.learned_frac <= 1.f))
         return set_err(nullptr, RECON_EINVAL, "learned_frac outside [0, 1]");
     if (o.seed_mode != RECON_SEED_RANDOM && o.seed_mode != RECON_SEED_LEARNED)

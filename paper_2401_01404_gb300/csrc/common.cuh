@@ -183,7 +183,14 @@ struct GaussView {
 
 struct ScoreParams {
     float lambda, w_clamp, h_clamp;
+    int grad_only;  // score by |d log pi / dW_ij| instead of the exact gain
 };
+
+// |d log pi / dW_ij| from the smooth part's derivative D at the current W_ij = W0
+// (the penalty contributes lambda sign(W0); nothing at W0 = 0)
+__device__ __forceinline__ float grad_dist(float D, float W0, float lambda) {
+    return fabsf(W0 == 0.f ? D : D - (W0 > 0.f ? lambda : -lambda));
+}
 
 // ---------------------------------------------------------------------------
 // growable device buffer
@@ -245,7 +252,11 @@ struct recon_ctx {
         return IsingView{xbits, phi, t, h, H, (int)N, (int)M, (int)Mp, (int)Mw};
     }
     GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
-    ScoreParams sp() const { return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp}; }
+    bool force_exact = false;  // exact gains even in gradient-distance mode (proposal targets)
+    ScoreParams sp() const {
+        return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp,
+                           opt.distance == RECON_DIST_GRADIENT && !force_exact ? 1 : 0};
+    }
 };
 
 // the context whose API call is running on this thread (for launch counting)

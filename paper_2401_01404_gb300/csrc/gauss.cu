@@ -133,8 +133,11 @@ __global__ void __launch_bounds__(256) k_gscore(GaussView v, WTable W, ScorePara
         float a = gauss_a(v, i, j, lane);
         float b = v.s2[i] * v.Q[j] + v.s2[j] * v.Q[i];
         float W0 = wt_lookup(W, pair_key(i, j));
-        float g, w;
-        gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
+        float g, w = W0;
+        if (p.grad_only)
+            g = grad_dist(a, W0, p.lambda);
+        else
+            gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
         if (lane == 0) {
             d_out[q] = -g;
             if (w_out) w_out[q] = w;
@@ -188,7 +191,10 @@ __global__ void k_gscore_seg(GaussView v, WTable W, ScoreParams p, const int32_t
         const float b = s2x * v.Q[gj] + v.s2[gj] * Qx;
         const float W0 = wt_lookup(W, pair_key(gx, gj));
         float g, w;
-        gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
+        if (p.grad_only)
+            g = grad_dist(a, W0, p.lambda);
+        else
+            gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
         if (lane == 0) d_out[pos] = -g;
     }
 }

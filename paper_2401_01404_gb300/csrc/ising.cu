@@ -438,8 +438,11 @@ __global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreP
         pass0_staged(st, sx, sb, Tj, Bj, v.Mw, lane, su, sv, dis);
         SmemRows R{st, sb, Tj, Bj, v.Mw, lane};
         float g, w;
-        int passes;
-        solve_from_pass0(R, v.Mp, su, sv, dis, Hx + Hj, W0, p.lambda, p.w_clamp, g, w, passes);
+        int passes = 0;
+        if (p.grad_only)
+            g = grad_dist(2.f * (float)(v.Mp - 2 * dis) - su - sv, W0, p.lambda);
+        else
+            solve_from_pass0(R, v.Mp, su, sv, dis, Hx + Hj, W0, p.lambda, p.w_clamp, g, w, passes);
         if (lane == 0) {
             d_out[pos] = -g;
             npass += (unsigned long long)passes;
@@ -464,9 +467,15 @@ __global__ void __launch_bounds__(256) k_score(IsingView v, WTable W, ScoreParam
         RS R;
         R.load(v, i, j, lane);
         float W0 = wt_lookup(W, pair_key(i, j));
-        float g, w;
-        int passes;
-        solve_pair(R, v.Mp, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
+        float g, w = W0;
+        int passes = 0;
+        float su, sv;
+        int dis;
+        pass0(R, su, sv, dis);
+        if (p.grad_only)
+            g = grad_dist(2.f * (float)(v.Mp - 2 * dis) - su - sv, W0, p.lambda);
+        else
+            solve_from_pass0(R, v.Mp, su, sv, dis, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
         if (lane == 0) {
             d_out[q] = -g;
             if (w_out) w_out[q] = w;

@@ -279,6 +279,13 @@ extern "C" recon_status recon_proposal_train(recon_ctx *c, const recon_train_opt
     recon_default_train_opts(&o);
     if (opts) o = *opts;
     if (o.steps < 0 || !(o.lr > 0.f)) return set_err(c, RECON_EINVAL, "steps >= 0 and lr > 0 are required");
+    // the targets are exact gains whatever distance the search ranks by
+    struct ExactScores {
+        recon_ctx *c;
+        bool was;
+        ~ExactScores() { c->force_exact = was; }
+    } exact_guard{c, c->force_exact};
+    c->force_exact = true;
     recon_status st = ensure_prop(c, o.seed);
     if (st != RECON_OK) return st;
     Proposal &P = *c->prop;

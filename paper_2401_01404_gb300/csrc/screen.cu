@@ -372,10 +372,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN);
-            // fast path, 64 columns at a time: max |g| against the loosest
-            // threshold of the unit (thr - s max c_j); the exact per-column test
-            // only when that fires
-            bool any = false;
+            // 64 columns at a time from registers: max |g| against the unit's loosest
+            // threshold (thr - s max c_j); only a thread whose row passes that test
+            // checks its 64 columns exactly, counts its survivors, reserves their
+            // slots with one atomic and writes them
 #pragma unroll 1
             for (int hf = 0; hf < BN / 64; ++hf) {
                 uint32_t r[64];
@@ -387,61 +387,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
 #pragma unroll
                 for (int q = 0; q < 64; ++q) m = fmaxf(m, fabsf(__uint_as_float(r[q])));
                 if (m + sc * cmax > thr) {
+                    // exact test of the 64 columns as a bit mask (branch-free), then
+                    // j > i, j < n and the stored couplings, then one reservation
                     const float4 *c4p = (const float4 *)(cn + 64 * hf);
+                    const int j0 = jt_cur + 64 * hf;
+                    unsigned long long mk = 0;
 #pragma unroll
                     for (int q4 = 0; q4 < 16; ++q4) {
                         const float4 c4 = c4p[q4];
-                        any |= fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr;
-                        any |= fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr;
-                        any |= fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr;
-                        any |= fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr;
+                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr) << (4 * q4 + 0);
+                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr) << (4 * q4 + 1);
+                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr) << (4 * q4 + 2);
+                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr) << (4 * q4 + 3);
                     }
-                }
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                // rare path (diagonal units, units holding a survivor): each thread
-                // counts its row's survivors, one scan and one atomic reserve the
-                // warp's slots, then each thread writes its own
-                int mine = 0;
-                unsigned long long base = 0;
-                for (int pass = 0; pass < 2; ++pass) {
-                    int w = 0;
-                    for (int c = 0; c < BN / 32; ++c) {
-                        uint32_t r[32];
-                        TMEM_LD32(r, taddr + (uint32_t)(32 * c));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            const int j = jt_cur + 32 * c + q;
-                            bool keep = i < j && j < a.n &&
-                                        fabsf(__uint_as_float(r[q])) + sc * cn[32 * c + q] > thr;
-                            if (keep && a.skip_stored) keep = !wt_contains(a.W, pair_key(i, j));  // stored couplings come separately
-                            if (keep) {
-                                if (pass == 1) {
-                                    const int64_t pos = (int64_t)base + w;
-                                    if (pos < a.cap) {
-                                        a.out[2 * pos] = i;
-                                        a.out[2 * pos + 1] = j;
-                                    }
-                                }
-                                ++w;
+                    const int below = i - j0;  // columns q <= below have j <= i
+                    if (below >= 63)
+                        mk = 0;
+                    else if (below >= 0)
+                        mk &= ~0ull << (below + 1);
+                    const int valid = a.n - j0;  // columns q < valid have j < n
+                    if (valid <= 0)
+                        mk = 0;
+                    else if (valid < 64)
+                        mk &= ~0ull >> (64 - valid);
+                    if (a.skip_stored) {  // stored couplings come separately
+                        for (unsigned long long mm = mk; mm; mm &= mm - 1) {
+                            const int q = __ffsll((long long)mm) - 1;
+                            if (wt_contains(a.W, pair_key(i, j0 + q))) mk &= ~(1ull << q);
+                        }
+                    }
+                    if (mk) {
+                        int64_t pos = (int64_t)atomicAdd(a.count, (unsigned long long)__popcll(mk));
+                        for (; mk; mk &= mk - 1, ++pos) {
+                            const int q = __ffsll((long long)mk) - 1;
+                            if (pos < a.cap) {
+                                a.out[2 * pos] = i;
+                                a.out[2 * pos + 1] = j0 + q;
                             }
                         }
-                    }
-                    if (pass == 0) {
-                        mine = w;
-                        int incl = w;  // inclusive scan over the warp
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += y;
-                        }
-                        const int total = __shfl_sync(0xffffffffu, incl, 31);
-                        if (total == 0) break;
-                        unsigned long long wb = 0;
-                        if (lane == 31) wb = atomicAdd(a.count, (unsigned long long)total);
-                        wb = __shfl_sync(0xffffffffu, wb, 31);
-                        base = wb + (unsigned long long)(incl - mine);
                     }
                 }
             }

@@ -20,6 +20,7 @@ RECON_ISING, RECON_GAUSSIAN = 0, 1
 RECON_X_INT8, RECON_X_FP32 = 0, 1
 RECON_KNN_NNDESCENT, RECON_KNN_EXHAUSTIVE, RECON_KNN_AUTO, RECON_KNN_SCREEN = 0, 1, 2, 3
 RECON_SEED_RANDOM, RECON_SEED_SCREEN, RECON_SEED_LEARNED = 0, 1, 2
+RECON_DIST_GAIN, RECON_DIST_GRADIENT = 0, 1
 STATUS_NAMES = ["RECON_OK", "RECON_EINVAL", "RECON_ENOMEM", "RECON_ECUDA", "RECON_ETIMEOUT", "RECON_ESTATE",
                 "RECON_EUNSUPPORTED"]
 
@@ -29,7 +30,7 @@ class recon_options(C.Structure):
                 ("max_knn_iters", C.c_int32), ("w_clamp", C.c_float), ("h_clamp", C.c_float),
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
                 ("timing", C.c_int32), ("no_graphs", C.c_int32),
-                ("learned_frac", C.c_float), ("reserved", C.c_int32 * 5)]
+                ("learned_frac", C.c_float), ("distance", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class recon_stats(C.Structure):

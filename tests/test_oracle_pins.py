@@ -237,6 +237,55 @@ def test_gcd_with_all_pairs_selects_what_cd_updates(oracle):
 # ---------------------------------------------------------------- Gaussian
 
 
+def _fd_slopes(o, set_state, W, pairs, eps=1e-5):
+    """Central differences of the oracle's objective along each W_ij (= W_ji)."""
+    out = []
+    for i, j in pairs.tolist():
+        vals = []
+        for sgn in (1.0, -1.0):
+            W2 = W.copy()
+            W2[i, j] += sgn * eps
+            W2[j, i] += sgn * eps
+            set_state(W2)
+            vals.append(o.objective())
+        out.append((vals[0] - vals[1]) / (2 * eps))
+    set_state(W)
+    return np.array(out)
+
+
+def test_ising_gradient_distance_is_the_objective_slope(oracle):
+    """The gradient distance (App. B) equals the slope of log pi along W_ij, at
+    zero and at nonzero couplings (where the prior adds -lam sign W_ij)."""
+    N, M, lam = 9, 40, 3.0
+    X = _rand_spins(N, M, 31)
+    W = _rand_W(N, 32, p=0.4, scale=0.3)
+    h = np.random.default_rng(33).normal(0, 0.2, N)
+    o = oracle.IsingOracle(X, lam=lam)
+    o.set_state(W, h)
+    pairs = oracle.all_pairs(np.arange(N))
+    wc = W[pairs[:, 0], pairs[:, 1]]
+    assert (wc != 0).sum() >= 5 and (wc == 0).sum() >= 5
+    g = oracle.ising_grad_rows(X, o.phi, pairs, lam, wcur=wc)
+    fd = _fd_slopes(o, lambda W2: o.set_state(W2, h), W, pairs)
+    assert np.allclose(g, np.abs(fd), rtol=1e-6, atol=1e-6)
+
+
+def test_gauss_gradient_distance_is_the_objective_slope(oracle):
+    N, M, lam = 8, 35, 0.9
+    g0 = np.random.default_rng(41)
+    X = g0.normal(0, 1, (N, M))
+    W = _rand_W(N, 42, p=0.4, scale=0.2, diag=9.0)
+    s2 = g0.uniform(0.4, 1.3, N)
+    o = oracle.GaussOracle(X, lam=lam)
+    o.set_state(W, s2)
+    pairs = oracle.all_pairs(np.arange(N))
+    wc = W[pairs[:, 0], pairs[:, 1]]
+    assert (wc != 0).sum() >= 5 and (wc == 0).sum() >= 5
+    g = oracle.gauss_grad_rows(X, o.mu, s2, pairs, lam, wcur=wc)
+    fd = _fd_slopes(o, lambda W2: o.set_state(W2, s2), W, pairs)
+    assert np.allclose(g, np.abs(fd), rtol=1e-6, atol=1e-6)
+
+
 def test_gauss_objective_matches_normal_logpdf(oracle):
     from scipy.stats import norm
 
