@@ -51,6 +51,10 @@ def _args():
     ap.add_argument("--scale-caps", type=int, default=8)
     ap.add_argument("--screen-bench", type=int, nargs=2, metavar=("N", "M"), default=None,
                     help="time only the tensor-core screen on N nodes x M seeded random spins")
+    ap.add_argument("--findbest-scaling", type=int, nargs="*", metavar="N", default=None,
+                    help="FindBest runtime against N on the paper's synthetic Gaussian (M = 10)")
+    ap.add_argument("--convergence", type=int, nargs="*", metavar="N", default=None,
+                    help="GCD against CD convergence on the paper's synthetic Gaussian (M = 100)")
     return ap.parse_args()
 
 
@@ -553,10 +557,155 @@ def run_screen_bench(a):
                       "data": "seeded uniform random spins"}), flush=True)
 
 
+def _paper_gaussian(N, M, seed):
+    """The paper's synthetic Gaussian: ER mean degree 5, off-diagonal precision
+    ~ N(-10^3, 10^2), W_ii = sum |W_ij| / (1 - 10^-3)^2; M exact samples
+    (float32, sample-major) and the penalty c sqrt(2 M ln N) sigma^2 with c = 2
+    and sigma^2 the median per-node variance (the tail bound on |a_ij| of an
+    unrelated pair, whose spread is 2 sqrt(M) sigma_i sigma_j)."""
+    from paper_2401_01404_gb300 import inputs
+
+    e, w, d = inputs.gaussian_er_precision(N, 5, -1000.0, 10.0, 1e-3, seed)
+    X = inputs.gaussian_precision_samples(N, e, w, d, M, seed, device="cuda")
+    var = float(np.median((X * X).mean(axis=1)))
+    lam = 2.0 * math.sqrt(2.0 * M * math.log(N)) * var
+    return np.ascontiguousarray(X.T.astype(np.float32)), lam, len(e)
+
+
+def run_findbest_scaling(a):
+    """FindBest (Algorithm 3 over NNDescent) on the paper's runtime workload
+    (M = 10) for growing N and several kappa (k = ceil(4m/N) = 4 kappa), next to
+    exhaustive scoring of all pairs (up to 5 10^4 nodes), with NNDescent's recall
+    of the exhaustive best pairs.  The penalty is 0: with M = 10 a penalty at
+    the sparsity level exceeds every attainable |a_ij| <= 2 M sigma_i sigma_j, and
+    at lambda = 0 every pair has the gain a^2 / (2 b) > 0 (the exact screen keeps
+    every pair there, so it is not the baseline). One JSON line."""
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon as R
+
+    sizes = a.findbest_scaling or [1000, 10000, 100000, 1000000]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    rows = []
+    for N in sizes:
+        Xs, _, E = _paper_gaussian(N, 10, 7000 + N)
+        X = torch.from_numpy(Xs).cuda()
+        row = {"N": N, "edges": E, "lambda": 0.0}
+        # kappa = 10 means lists of 40 (candidate buffers of n (2k)^2 pairs): up to 10^5 nodes
+        for kappa in ((1.0, 10.0) if N <= 100000 else (1.0,)):
+            m = int(math.floor(kappa * N + 0.5))
+            ent = {}
+            c = R.Recon(X, R.RECON_GAUSSIAN, stream=stream, lam=0.0, seed=3)
+            (p, d), ent["findbest_s"] = timed(lambda: c.best_pairs(1, kappa))
+            st = c.stats()
+            ent.update({"levels": st["levels"], "knn_iters": st["knn_iters"], "pair_evals": st["pair_evals"]})
+            if N <= 50000:  # the exhaustive k-NN holds a dense N x N score matrix
+                (pe, de), ent["exhaustive_s"] = timed(lambda: c.exhaustive_best(m))
+                ent["recall_vs_exhaustive"] = len({tuple(x) for x in pe.tolist()} & {tuple(x) for x in p.tolist()}) / m
+            c.close()
+            row[f"kappa{int(kappa)}"] = ent
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    fit = {}
+    for kappa in (1, 10):
+        sel = [r for r in rows if f"kappa{kappa}" in r]
+        n = np.array([r["N"] for r in sel], dtype=float)
+        t = np.array([r[f"kappa{kappa}"]["findbest_s"] for r in sel])
+        if len(n) >= 2:
+            fit[f"kappa{kappa}_loglog_slope"] = float(np.polyfit(np.log(n), np.log(t), 1)[0])
+            fit[f"kappa{kappa}_t_over_NlogN2"] = (t / (n * np.log(n) ** 2)).tolist()
+    print(json.dumps({"findbest_scaling": rows, "fit": fit, "M": 10,
+                      "data": "paper's synthetic Gaussian (ER deg 5, W_ij ~ N(-1e3, 10^2))"}), flush=True)
+
+
+def run_convergence(a):
+    """Algorithm 2 (GCD, FindBest by the exact screen or by NNDescent) against
+    coordinate descent on all pairs, objective against wall time, on the
+    paper's convergence workload (M = 100). CD iteration: every pair scored
+    exhaustively, the pairs with a positive gain updated in order of gain, then
+    the diagonal; GCD iteration: recon_gcd_step(k, kappa). One JSON line."""
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon as R
+
+    sizes = a.convergence or [100, 1000, 10000]
+    stream = torch.cuda.current_stream()
+    out = []
+    for N in sizes:
+        Xs, lam, E = _paper_gaussian(N, 100, 9000 + N)
+        X = torch.from_numpy(Xs).cuda()
+        res = {"N": N, "edges": E, "lambda": lam}
+
+        def run(tag, step, max_it):
+            ctx = R.Recon(X, R.RECON_GAUSSIAN, stream=stream, lam=lam, **step.get("opts", {}))
+            traj, t = [(0.0, ctx.objective())], 0.0
+            for _ in range(max_it):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                step["fn"](ctx)
+                torch.cuda.synchronize()
+                t += time.perf_counter() - t0
+                traj.append((t, ctx.objective()))
+                if abs(traj[-1][1] - traj[-2][1]) <= 1e-9 * abs(traj[-1][1]):
+                    break
+            ctx.close()
+            res[tag] = traj
+
+        # every pair is scored; the positive-gain ones (far fewer than 100 N) come back
+        m_cd = min(N * (N - 1) // 2, 100 * N)
+
+        def cd(ctx):
+            p, d = ctx.exhaustive_best(m_cd)
+            if len(d) == m_cd and d[-1] < 0 and m_cd < N * (N - 1) // 2:
+                raise RuntimeError("more positive-gain pairs than the CD selection holds")
+            sel = p[d < 0]
+            dl = ctx.cd_sweep(sel) if len(sel) else 0.0
+            return dl + ctx.field_sweep()
+
+        run("cd", {"fn": cd}, 60)
+        for kappa in (0.25, 1.0, 4.0):
+            run(f"gcd_screen_kappa{kappa:g}", {"fn": lambda c, k=kappa: c.gcd_step(1, k)[0],
+                                                 "opts": {"knn_mode": R.RECON_KNN_SCREEN}}, 400)
+        run("gcd_nndescent_kappa1", {"fn": lambda c: c.gcd_step(1, 1.0)[0]}, 400)
+        best = max(v[-1][1] for k, v in res.items() if isinstance(v, list))
+        tol = 1e-6 * abs(best)
+        res["time_to_optimum"] = {k: next((t for t, o in v if o >= best - tol), None)
+                                  for k, v in res.items() if isinstance(v, list)}
+        res["iterations"] = {k: len(v) - 1 for k, v in res.items() if isinstance(v, list)}
+        print(json.dumps({"N": N, "time_to_optimum": res["time_to_optimum"], "iterations": res["iterations"],
+                          "objective_best": best}), flush=True)
+        for k in list(res):
+            if isinstance(res[k], list) and len(res[k]) > 40:  # keep the line short
+                v = res[k]
+                res[k] = v[:: max(1, len(v) // 40)] + [v[-1]]
+        out.append(res)
+    print(json.dumps({"convergence": out, "M": 100}), flush=True)
+
+
 def main():
     a = _args()
     if a.screen_bench:
         run_screen_bench(a)
+        return
+    if a.findbest_scaling is not None:
+        run_findbest_scaling(a)
+        return
+    if a.convergence is not None:
+        run_convergence(a)
         return
     if a.impl == "reference":
         run_reference(a)

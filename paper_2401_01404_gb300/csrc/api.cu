@@ -450,15 +450,23 @@ static recon_status cd_sweep_dev(recon_ctx *c, const int32_t *dp, int64_t P, dou
     }
     recon_status st = table_reserve(c, P);
     if (st != RECON_OK) return st;
-    ENSURE(BUF_FIRST, sizeof(int) * c->N);
     ENSURE(BUF_BATCH, sizeof(int) * P);
     ENSURE(BUF_ORDER, sizeof(int) * P);
     ENSURE(BUF_OFF, sizeof(int) * (P + 2));
     ENSURE(BUF_DELTA, sizeof(double) * (P + 1));
     ENSURE(BUF_TMP2, sizeof(int) * 2);
+    ENSURE(BUF_SORT0, sizeof(unsigned long long) * 2 * P);
+    ENSURE(BUF_SORT1, sizeof(unsigned long long) * 2 * P);
+    ENSURE(BUF_SORT2, sizeof(uint32_t) * 4 * P);
+    ENSURE(BUF_SORT3, sizeof(int64_t) * layer_tmp_elems(P));
+    ENSURE(BUF_SORT4, sizeof(int32_t) * 5 * P);
     int *nb_dev = buf<int>(c, BUF_TMP2);
-    CK(launch_layer_batches(dp, P, (int)c->N, buf<int>(c, BUF_FIRST), buf<int>(c, BUF_BATCH), buf<int>(c, BUF_ORDER),
-                            buf<int>(c, BUF_OFF), nb_dev, c->cnt, c->stream));
+    int32_t *links = buf<int32_t>(c, BUF_SORT4);
+    uint32_t *vals = buf<uint32_t>(c, BUF_SORT2);
+    CK(launch_layer_frontier(dp, P, (int)c->N, buf<unsigned long long>(c, BUF_SORT0),
+                             buf<unsigned long long>(c, BUF_SORT1), vals, vals + 2 * P, buf<int64_t>(c, BUF_SORT3),
+                             links, links + 2 * P, links + 3 * P, links + 4 * P, buf<int>(c, BUF_BATCH),
+                             buf<int>(c, BUF_ORDER), buf<int>(c, BUF_OFF), nb_dev, c->stream));
     int nb = 0;
     CK(cudaMemcpyAsync(&nb, nb_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -466,13 +474,28 @@ static recon_status cd_sweep_dev(recon_ctx *c, const int32_t *dp, int64_t P, dou
     CK(cudaMemcpyAsync(off.data(), buf<int>(c, BUF_OFF), sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     double *delta = buf<double>(c, BUF_DELTA);
-    for (int b = 0; b < nb; ++b) {
+    const int *offd = buf<int>(c, BUF_OFF), *order = buf<int>(c, BUF_ORDER);
+    // a batch with at most `thin` pairs joins a run of thin batches that one block
+    // applies in turn (block barriers between them); a wider batch gets a grid
+    const int thin = c->model == RECON_ISING ? 8 : 64;
+    for (int b = 0; b < nb;) {
+        if (off[b + 1] - off[b] > thin) {
+            if (c->model == RECON_ISING)
+                CK(launch_ising_update(c->iv(), c->W, c->sp(), dp, order, off[b], off[b + 1], delta, c->cnt,
+                                       c->stream));
+            else
+                CK(launch_gauss_update(c->gv(), c->W, c->sp(), dp, order, off[b], off[b + 1], delta, c->cnt,
+                                       c->stream));
+            ++b;
+            continue;
+        }
+        int e = b;
+        while (e < nb && off[e + 1] - off[e] <= thin) ++e;
         if (c->model == RECON_ISING)
-            CK(launch_ising_update(c->iv(), c->W, c->sp(), dp, buf<int>(c, BUF_ORDER), off[b], off[b + 1], delta,
-                                   c->cnt, c->stream));
+            CK(launch_ising_update_rounds(c->iv(), c->W, c->sp(), dp, order, offd, b, e, delta, c->cnt, c->stream));
         else
-            CK(launch_gauss_update(c->gv(), c->W, c->sp(), dp, buf<int>(c, BUF_ORDER), off[b], off[b + 1], delta,
-                                   c->cnt, c->stream));
+            CK(launch_gauss_update_rounds(c->gv(), c->W, c->sp(), dp, order, offd, b, e, delta, c->cnt, c->stream));
+        b = e;
     }
     c->stats.pair_evals += P;
     CK(launch_sum_doubles(delta, P, delta + P, c->stream));

@@ -323,9 +323,17 @@ cudaError_t launch_gauss_diag_sweep(GaussView v, double *delta, cudaStream_t s);
 // util.cu
 cudaError_t launch_penalty(WTable W, double *out, cudaStream_t s);
 cudaError_t launch_sum_doubles(const double *in, int64_t n, double *out, cudaStream_t s);
-cudaError_t launch_layer_batches(const int32_t *pairs, int64_t P, int N, int *first, int *batch,
-                                 int *order, int *boff, int *nb, unsigned long long *cnt,
-                                 cudaStream_t s);
+int64_t layer_tmp_elems(int64_t P);
+cudaError_t launch_layer_frontier(const int32_t *pairs, int64_t P, int N, unsigned long long *keys,
+                                  unsigned long long *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t *tmp,
+                                  int32_t *succ, int32_t *indeg, int32_t *fa, int32_t *fb, int *batch, int *order,
+                                  int *boff, int *nb, cudaStream_t s);
+cudaError_t launch_ising_update_rounds(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                       const int32_t *order, const int32_t *off, int b0, int b1, double *delta,
+                                       unsigned long long *cnt, cudaStream_t s);
+cudaError_t launch_gauss_update_rounds(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                       const int32_t *order, const int32_t *off, int b0, int b1, double *delta,
+                                       unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
 cudaError_t launch_table_count(WTable W, unsigned long long *out, cudaStream_t s);

@@ -91,12 +91,16 @@ __global__ void k_gobjective(GaussView v, double *partials) {
 }
 
 // a = -sum (e_i x_j + e_j x_i), over float4 chunks (Mp is a multiple of 32)
+// coherent = true reads e with plain loads (rows that an earlier batch of the
+// same launch may have written; the read-only path could be stale)
+template <bool coherent = false>
 __device__ __forceinline__ float gauss_a(const GaussView &v, int i, int j, int lane) {
     const float4 *xi = (const float4 *)(v.xg + (int64_t)i * v.Mp), *xj = (const float4 *)(v.xg + (int64_t)j * v.Mp);
     const float4 *ei = (const float4 *)(v.e + (int64_t)i * v.Mp), *ej = (const float4 *)(v.e + (int64_t)j * v.Mp);
     float acc = 0.f;
     for (int q = lane; q < v.Mp / 4; q += 32) {
-        float4 a = __ldg(ei + q), b = __ldg(xj + q), c = __ldg(ej + q), d = __ldg(xi + q);
+        float4 a = coherent ? ei[q] : __ldg(ei + q), b = __ldg(xj + q), c = coherent ? ej[q] : __ldg(ej + q),
+               d = __ldg(xi + q);
         acc = fmaf(a.x, b.x, acc);
         acc = fmaf(a.y, b.y, acc);
         acc = fmaf(a.z, b.z, acc);
@@ -199,17 +203,14 @@ __global__ void k_gscore_seg(GaussView v, WTable W, ScoreParams p, const int32_t
     }
 }
 
-__global__ void __launch_bounds__(256) k_gupdate(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
-                                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
-                                                 unsigned long long *cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (q >= end) return;
-    const int pidx = order[q];
+// One pair of Algorithm 2's update loop (closed-form maximiser), then rows i
+// and j of mu and e and the stored coupling (one warp).
+__device__ __forceinline__ void gupdate_one(GaussView v, WTable W, ScoreParams p, const int32_t *pairs, int pidx,
+                                            double *delta, unsigned long long *cnt, int lane) {
     const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
     const uint64_t key = pair_key(i, j);
     const float W0 = wt_lookup(W, key);
-    float a = gauss_a(v, i, j, lane);
+    float a = gauss_a<true>(v, i, j, lane);
     float b = v.s2[i] * v.Q[j] + v.s2[j] * v.Q[i];
     float g, w;
     gauss_solve(a, b, W0, p.lambda, p.w_clamp, g, w);
@@ -228,6 +229,26 @@ __global__ void __launch_bounds__(256) k_gupdate(GaussView v, WTable W, ScorePar
         if (lane == 0 && !wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
     }
     if (lane == 0) delta[pidx] = fabs((double)dl);
+}
+
+__global__ void __launch_bounds__(256) k_gupdate(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
+                                                 unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (q >= end) return;
+    gupdate_one(v, W, p, pairs, order[q], delta, cnt, lane);
+}
+
+// Consecutive thin batches b0 .. b1-1 in one block, separated by block barriers.
+__global__ void __launch_bounds__(1024) k_gupdate_rounds(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                         const int32_t *order, const int32_t *off, int b0, int b1,
+                                                         double *delta, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = b0; b < b1; ++b) {
+        for (int q = off[b] + warp; q < off[b + 1]; q += nw) gupdate_one(v, W, p, pairs, order[q], delta, cnt, lane);
+        __syncthreads();
+    }
 }
 
 __global__ void k_gdiag(GaussView v, double *delta) {
@@ -317,6 +338,14 @@ cudaError_t launch_gauss_update(GaussView v, WTable W, ScoreParams p, const int3
                                 cudaStream_t s) {
     if (end <= begin) return cudaSuccess;
     k_gupdate<<<grid_for(end - begin), 256, 0, s>>>(v, W, p, pairs, order, begin, end, delta, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_update_rounds(GaussView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                       const int32_t *order, const int32_t *off, int b0, int b1, double *delta,
+                                       unsigned long long *cnt, cudaStream_t s) {
+    if (b1 <= b0) return cudaSuccess;
+    k_gupdate_rounds<<<1, 1024, 0, s>>>(v, W, p, pairs, order, off, b0, b1, delta, cnt); note_launch();
     return cudaGetLastError();
 }
 

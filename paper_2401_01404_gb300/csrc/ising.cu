@@ -32,6 +32,9 @@ struct RegRows {  // both rows in registers (NW words of 32 samples)
     float ti[NW], tj[NW];
     uint32_t pi, pj;  // bit c: x = -1 at sample 32c + lane
     int Mw;
+    // coherent = true reads t with plain loads: rows that an earlier batch of
+    // the same launch may have written (the read-only path could be stale)
+    template <bool coherent = false>
     __device__ __forceinline__ void load(const IsingView &v, int i, int j, int lane) {
         Mw = v.Mw;
         const float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
@@ -40,8 +43,8 @@ struct RegRows {  // both rows in registers (NW words of 32 samples)
 #pragma unroll
         for (int c = 0; c < NW; ++c) {
             if (c < Mw) {
-                ti[c] = __ldg(Ti + 32 * c + lane);
-                tj[c] = __ldg(Tj + 32 * c + lane);
+                ti[c] = coherent ? Ti[32 * c + lane] : __ldg(Ti + 32 * c + lane);
+                tj[c] = coherent ? Tj[32 * c + lane] : __ldg(Tj + 32 * c + lane);
                 pi |= ((__ldg(Bi + c) >> lane) & 1u) << c;
                 pj |= ((__ldg(Bj + c) >> lane) & 1u) << c;
             } else {
@@ -62,17 +65,20 @@ struct GlobRows {  // rows re-read every pass
     const float *Ti, *Tj;
     const uint32_t *Bi, *Bj;
     int Mw, lane;
+    bool coh;  // plain loads of t (rows written earlier in the same launch)
+    template <bool coherent = false>
     __device__ __forceinline__ void load(const IsingView &v, int i, int j, int l) {
         Mw = v.Mw;
         lane = l;
+        coh = coherent;
         Ti = v.t + (int64_t)i * v.Mp;
         Tj = v.t + (int64_t)j * v.Mp;
         Bi = v.xbits + (int64_t)i * v.Mw;
         Bj = v.xbits + (int64_t)j * v.Mw;
     }
     __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb) const {
-        a = __ldg(Ti + 32 * c + lane);
-        b = __ldg(Tj + 32 * c + lane);
+        a = coh ? Ti[32 * c + lane] : __ldg(Ti + 32 * c + lane);
+        b = coh ? Tj[32 * c + lane] : __ldg(Tj + 32 * c + lane);
         sa = (__ldg(Bi + c) << (31 - lane)) & 0x80000000u;
         sb = (__ldg(Bj + c) << (31 - lane)) & 0x80000000u;
     }
@@ -485,19 +491,14 @@ __global__ void __launch_bounds__(256) k_score(IsingView v, WTable W, ScoreParam
     if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
 }
 
-// One matching batch of Algorithm 2's updates: pairs order[begin..end) share no
-// node, so their row updates are independent.
+// One pair of Algorithm 2's update loop: its 1-D maximiser, then rows i and j
+// of phi and t, H_i, H_j and the stored coupling (one warp).
 template <class RS>
-__global__ void __launch_bounds__(256) k_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
-                                                const int32_t *order, int64_t begin, int64_t end,
-                                                double *delta, unsigned long long *cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (q >= end) return;
-    const int pidx = order[q];
+__device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, int pidx,
+                                           double *delta, unsigned long long *cnt, int lane) {
     const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
     RS R;
-    R.load(v, i, j, lane);
+    R.template load<true>(v, i, j, lane);
     const uint64_t key = pair_key(i, j);
     const float W0 = wt_lookup(W, key);
     float g, w;
@@ -534,6 +535,32 @@ __global__ void __launch_bounds__(256) k_update(IsingView v, WTable W, ScorePara
     if (lane == 0) {
         delta[pidx] = fabs((double)dl);
         atomicAdd(&cnt[CNT_NEWTON], (unsigned long long)passes);
+    }
+}
+
+// One matching batch of the update loop: pairs order[begin..end) share no node,
+// so their row updates are independent.
+template <class RS>
+__global__ void __launch_bounds__(256) k_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                const int32_t *order, int64_t begin, int64_t end,
+                                                double *delta, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (q >= end) return;
+    update_one<RS>(v, W, p, pairs, order[q], delta, cnt, lane);
+}
+
+// Consecutive thin batches b0 .. b1-1 in one block: the batches run in turn,
+// separated by block barriers (which also order the row writes of one batch
+// before the reads of the next), each spread over the block's warps.
+template <class RS>
+__global__ void __launch_bounds__(256) k_update_rounds(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                       const int32_t *order, const int32_t *off, int b0, int b1,
+                                                       double *delta, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = b0; b < b1; ++b) {
+        for (int q = off[b] + warp; q < off[b + 1]; q += nw) update_one<RS>(v, W, p, pairs, order[q], delta, cnt, lane);
+        __syncthreads();
     }
 }
 
@@ -702,6 +729,14 @@ cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int3
     if (end <= begin) return cudaSuccess;
     unsigned grid = grid_for(end - begin);
     DISPATCH_ROWS(v.Mw, (k_update<RS><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, end, delta, cnt))); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_update_rounds(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                       const int32_t *order, const int32_t *off, int b0, int b1, double *delta,
+                                       unsigned long long *cnt, cudaStream_t s) {
+    if (b1 <= b0) return cudaSuccess;
+    DISPATCH_ROWS(v.Mw, (k_update_rounds<RS><<<1, 256, 0, s>>>(v, W, p, pairs, order, off, b0, b1, delta, cnt))); note_launch();
     return cudaGetLastError();
 }
 

@@ -91,65 +91,87 @@ __global__ void k_table_rehash(WTable from, WTable to) {
     }
 }
 
-// -------- matching-batch layering -------------------------------------------
-// Pairs are taken in index order.  Round r takes every remaining pair that is
-// the first remaining pair at both of its endpoints; such pairs share no node.
-// A pair therefore lands in a later round than every earlier pair it shares a
-// node with, so applying the rounds in turn equals the sequential loop.  One
-// block; each round takes at least the first remaining pair, so at most P
-// rounds run.
-__global__ void __launch_bounds__(1024) k_layer(const int32_t *pairs, int64_t P, int *first, int *batch,
-                                                int *order, int *boff, int *nb_out) {
-    __shared__ int s_left, s_taken;
-    int64_t left = P;
-    int r = 0;
-    for (int64_t p = threadIdx.x; p < P; p += blockDim.x) batch[p] = -1;
+// -------- matching batches in O(P) -------------------------------------------
+// Algorithm 2's update loop in matching batches: a pair goes into the batch after
+// the latest batch holding an earlier pair that shares a node with it, so that
+// applying the batches in turn (the pairs of a batch share no node) equals the
+// sequential loop.  The batches are found through the per-node order of the pairs:
+// entry e = 2p + side stands for pair p at node pairs[e]; after a stable sort of
+// the entries by node, the entry that follows e at the same node is the next
+// pair there.  A pair's batch is one more than the latest batch among the
+// pairs before it at its two nodes, i.e. it joins the frontier after both its
+// predecessors have been placed.
+__global__ void k_node_entries(const int32_t *pairs, int64_t P, unsigned long long *keys, uint32_t *vals) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * P) return;
+    keys[e] = ((unsigned long long)(uint32_t)pairs[e] << 32) | (unsigned long long)(uint32_t)e;
+    vals[e] = (uint32_t)e;
+}
+
+__global__ void k_node_links(const unsigned long long *keys, int64_t n2, int32_t *succ, int32_t *indeg) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n2) return;
+    const unsigned long long cur = keys[k];
+    int32_t nxt = -1;
+    if (k + 1 < n2 && (keys[k + 1] >> 32) == (cur >> 32)) {
+        nxt = (int32_t)((uint32_t)keys[k + 1] >> 1);
+        atomicAdd(&indeg[nxt], 1);
+    }
+    succ[(uint32_t)cur] = nxt;
+}
+
+// One block.  Each pair enters exactly one frontier (links only go from a pair
+// to a later one), so the loop ends after at most P batches.
+__global__ void __launch_bounds__(1024) k_frontier(int64_t P, const int32_t *succ, int32_t *indeg, int *batch,
+                                                   int32_t *fa, int32_t *fb, int *nb_out) {
+    __shared__ int n_cur, n_next;
+    if (threadIdx.x == 0) n_cur = 0;
     __syncthreads();
-    while (left > 0) {
-        for (int64_t p = threadIdx.x; p < P; p += blockDim.x)
-            if (batch[p] < 0) {
-                atomicMin(&first[pairs[2 * p]], (int)p);
-                atomicMin(&first[pairs[2 * p + 1]], (int)p);
-            }
-        if (threadIdx.x == 0) s_taken = 0;
+    for (int64_t p = threadIdx.x; p < P; p += blockDim.x)
+        if (indeg[p] == 0) fa[atomicAdd(&n_cur, 1)] = (int32_t)p;
+    __syncthreads();
+    int r = 0;
+    int32_t *cur = fa, *nxt = fb;
+    while (n_cur > 0) {
+        if (threadIdx.x == 0) n_next = 0;
         __syncthreads();
-        int taken = 0;
-        for (int64_t p = threadIdx.x; p < P; p += blockDim.x)
-            if (batch[p] < 0 && first[pairs[2 * p]] == (int)p && first[pairs[2 * p + 1]] == (int)p) {
-                batch[p] = r;
-                ++taken;
+        const int nc = n_cur;
+        for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+            const int p = cur[q];
+            batch[p] = r;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int sc = succ[2 * p + side];
+                if (sc >= 0 && atomicSub(&indeg[sc], 1) == 1) nxt[atomicAdd(&n_next, 1)] = sc;
             }
-        atomicAdd(&s_taken, taken);
+        }
         __syncthreads();
-        for (int64_t p = threadIdx.x; p < P; p += blockDim.x)
-            if (batch[p] < 0 || batch[p] == r) {
-                first[pairs[2 * p]] = 0x7fffffff;
-                first[pairs[2 * p + 1]] = 0x7fffffff;
-            }
-        left -= s_taken;
+        if (threadIdx.x == 0) n_cur = n_next;
+        int32_t *t = cur;
+        cur = nxt;
+        nxt = t;
         ++r;
         __syncthreads();
     }
-    // counting sort by round (order within a round is free: its pairs are independent)
-    for (int b = threadIdx.x; b <= r; b += blockDim.x) boff[b] = 0;
+    if (threadIdx.x == 0) *nb_out = r;
+}
+
+// pairs grouped by batch (order within a batch is free: its pairs are
+// independent); boff[b] = the start of batch b, boff[nb] = P
+__global__ void __launch_bounds__(1024) k_batch_order(int64_t P, const int *batch, const int *nb_in, int *order,
+                                                      int *boff) {
+    const int nb = *nb_in;
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) boff[b] = 0;
     __syncthreads();
     for (int64_t p = threadIdx.x; p < P; p += blockDim.x) atomicAdd(&boff[batch[p] + 1], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < r; ++b) boff[b + 1] += boff[b];
-        *nb_out = r;
-        s_left = 0;
-    }
+    if (threadIdx.x == 0)
+        for (int b = 0; b < nb; ++b) boff[b + 1] += boff[b];
     __syncthreads();
-    // claim positions: boff[b] walks from the start to the end of round b
-    for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
-        int pos = atomicAdd(&boff[batch[p]], 1);
-        order[pos] = (int)p;
-    }
+    for (int64_t p = threadIdx.x; p < P; p += blockDim.x) order[atomicAdd(&boff[batch[p]], 1)] = (int)p;
     __syncthreads();
-    // boff[b] now holds the end of round b; shift to get the starts back
-    if (threadIdx.x == 0) {
-        for (int b = r; b > 0; --b) boff[b] = boff[b - 1];
+    if (threadIdx.x == 0) {  // boff[b] now holds the end of batch b
+        for (int b = nb; b > 0; --b) boff[b] = boff[b - 1];
         boff[0] = 0;
     }
 }
@@ -257,15 +279,6 @@ cudaError_t launch_sum_doubles(const double *in, int64_t n, double *out, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_layer_batches(const int32_t *pairs, int64_t P, int N, int *first, int *batch, int *order,
-                                 int *boff, int *nb, unsigned long long *cnt, cudaStream_t s) {
-    (void)cnt;
-    cudaError_t e = launch_fill_i32(first, 0x7fffffff, N, s);
-    if (e != cudaSuccess) return e;
-    k_layer<<<1, 1024, 0, s>>>(pairs, P, first, batch, order, boff, nb); note_launch();
-    return cudaGetLastError();
-}
-
 cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int64_t b = (n + 255) / 256;
@@ -368,4 +381,28 @@ cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned lo
     }
     *result_in_alt = alt;
     return cudaSuccess;
+}
+
+int64_t layer_tmp_elems(int64_t P) { return radix_tmp_elems(std::max<int64_t>(2 * P, 2)); }
+
+cudaError_t launch_layer_frontier(const int32_t *pairs, int64_t P, int N, unsigned long long *keys,
+                                  unsigned long long *keys_alt, uint32_t *vals, uint32_t *vals_alt, int64_t *tmp,
+                                  int32_t *succ, int32_t *indeg, int32_t *fa, int32_t *fb, int *batch, int *order,
+                                  int *boff, int *nb, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    const int64_t n2 = 2 * P;
+    const unsigned g2 = (unsigned)((n2 + 255) / 256);
+    k_node_entries<<<g2, 256, 0, s>>>(pairs, P, keys, vals); note_launch();
+    int bits = 8;
+    while (bits < 32 && ((int64_t)1 << bits) < (int64_t)N) bits += 8;
+    bool alt = false;
+    cudaError_t e = radix_sort_u64(keys, vals, keys_alt, vals_alt, n2, 32, 32 + bits, tmp, &alt, s);
+    if (e != cudaSuccess) return e;
+    const unsigned long long *sorted = alt ? keys_alt : keys;
+    e = cudaMemsetAsync(indeg, 0, sizeof(int32_t) * P, s);
+    if (e != cudaSuccess) return e;
+    k_node_links<<<g2, 256, 0, s>>>(sorted, n2, succ, indeg); note_launch();
+    k_frontier<<<1, 1024, 0, s>>>(P, succ, indeg, batch, fa, fb, nb); note_launch();
+    k_batch_order<<<1, 1024, 0, s>>>(P, batch, nb, order, boff); note_launch();
+    return cudaGetLastError();
 }

@@ -193,6 +193,71 @@ def gaussian_dense_samples(Q: np.ndarray, M: int, seed: int) -> np.ndarray:
 # workloads
 # ----------------------------------------------------------------------------
 
+def gaussian_er_precision(N: int, deg: float, mean: float, std: float, eps: float, seed: int):
+    """The paper's synthetic Gaussian model (its runtime and convergence
+    studies): off-diagonal precision entries on an Erdos-Renyi graph of mean
+    degree `deg`, each ~ N(mean, std^2), and W_ii = sum_j |W_ij| / (1 - eps)^2,
+    so W is diagonally dominant and positive definite.  A node without edges
+    would get W_ii = 0 (an improper variable); it takes the median diagonal of
+    the others, so that its variance is of the same order as theirs.
+    Returns (edges [E x 2], off-diagonal values [E], diagonal [N])."""
+    edges = erdos_renyi(N, deg, rng(seed, GRAPH))
+    w = rng(seed, COUPLINGS).normal(mean, std, len(edges))
+    rowsum = np.bincount(edges[:, 0], np.abs(w), minlength=N) + np.bincount(edges[:, 1], np.abs(w), minlength=N)
+    diag = rowsum / (1.0 - eps) ** 2
+    diag[rowsum == 0] = np.median(diag[rowsum > 0]) if (rowsum > 0).any() else 1.0
+    return edges, w, diag
+
+
+def gaussian_precision_samples(N: int, edges: np.ndarray, w: np.ndarray, diag: np.ndarray, M: int, seed: int,
+                               device: str = "cpu", tol: float = 1e-10, max_iter: int = 20000) -> np.ndarray:
+    """M exact samples of N(0, W^-1) for a sparse diagonally dominant W.
+    W = B^T B with one row sqrt|w_ij| (e_i + sign(w_ij) e_j) per edge and one row
+    sqrt(r_i) e_i per node (r_i = W_ii - sum_j |W_ij| >= 0), so b = B^T z with z
+    white noise is N(0, W), and x = W^-1 b is N(0, W^-1).  The M systems W x = b
+    are solved together by conjugate gradients in float64 (torch, on `device`)
+    to a relative residual of `tol`.  Returns float64, node-major (N x M)."""
+    import torch
+
+    dev = torch.device(device)
+    E = len(edges)
+    i = torch.as_tensor(edges[:, 0], device=dev)
+    j = torch.as_tensor(edges[:, 1], device=dev)
+    wt = torch.as_tensor(w, dtype=torch.float64, device=dev)
+    dg = torch.as_tensor(diag, dtype=torch.float64, device=dev)
+    absw = wt.abs()
+    r = dg - (torch.zeros(N, dtype=torch.float64, device=dev).index_add_(0, i, absw).index_add_(0, j, absw))
+    r = r.clamp_min(0.0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(rng(seed, SAMPLES).integers(0, 2**62)))
+    ze = torch.randn((E, M), generator=gen, dtype=torch.float64, device=dev)
+    zn = torch.randn((N, M), generator=gen, dtype=torch.float64, device=dev)
+    se = absw.sqrt().unsqueeze(1) * ze
+    b = r.sqrt().unsqueeze(1) * zn
+    b.index_add_(0, i, se)
+    b.index_add_(0, j, torch.sign(wt).unsqueeze(1) * se)
+    rows = torch.cat([i, j, torch.arange(N, device=dev)])
+    cols = torch.cat([j, i, torch.arange(N, device=dev)])
+    vals = torch.cat([wt, wt, dg])
+    Wm = torch.sparse_coo_tensor(torch.stack([rows, cols]), vals, (N, N), check_invariants=True).coalesce()
+    x = torch.zeros_like(b)
+    res = b.clone()
+    p = res.clone()
+    rr = (res * res).sum(0)
+    b2 = rr.clone()
+    for _ in range(max_iter):
+        if bool((rr <= tol * tol * b2).all()):
+            break
+        Ap = torch.sparse.mm(Wm, p)
+        alpha = rr / (p * Ap).sum(0)
+        x += alpha * p
+        res -= alpha * Ap
+        rr_new = (res * res).sum(0)
+        p = res + (rr_new / rr) * p
+        rr = rr_new
+    return x.cpu().numpy()
+
+
 @dataclass
 class Workload:
     name: str
