@@ -248,34 +248,34 @@ struct SmemRows {
     }
 };
 
-// pass 0 against a staged row: sv = sum x_i t_j (x_i as +-1 floats in shared
+// Pass 0 against a staged row: sv = sum x_i t_j (x_i as +-1 floats in shared
 // memory), su = sum x_j t_i (sign of t_i flipped by x_j's bit), and the count of
-// disagreeing spins by popcount of whole words.  Four words in flight per lane.
-__device__ __forceinline__ void pass0_staged(const float *st, const float *sx, const uint32_t *sb, const float *Tj,
-                                             const uint32_t *Bj, int Mw, int lane, float &su, float &sv, int &dis) {
+// disagreeing spins by popcount of whole words.  Every load of row j is issued
+// before any is used (NW >= Mw words, Mw <= 32): lane c holds word c of x_j's
+// bits and shares it by shuffle, so a candidate costs one round trip to L2.
+template <int NW>
+__device__ __forceinline__ void pass0_staged_all(const float *st, const float *sx, const uint32_t *sb,
+                                                 const float *Tj, const uint32_t *Bj, int Mw, int lane, float &su,
+                                                 float &sv, int &dis) {
+    float t[NW];
+    const uint32_t wl = lane < Mw ? __ldg(Bj + lane) : 0u;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) t[c] = c < Mw ? __ldg(Tj + 32 * c + lane) : 0.f;
+    const int d = lane < Mw ? __popc(sb[lane] ^ wl) : 0;
     float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-    int c = 0;
-    for (; c + 4 <= Mw; c += 4) {
-        float t0 = __ldg(Tj + 32 * c + lane), t1 = __ldg(Tj + 32 * (c + 1) + lane);
-        float t2 = __ldg(Tj + 32 * (c + 2) + lane), t3 = __ldg(Tj + 32 * (c + 3) + lane);
-        uint32_t w0 = __ldg(Bj + c), w1 = __ldg(Bj + c + 1), w2 = __ldg(Bj + c + 2), w3 = __ldg(Bj + c + 3);
-        b0 = fmaf(sx[32 * c + lane], t0, b0);
-        b1 = fmaf(sx[32 * (c + 1) + lane], t1, b1);
-        b0 = fmaf(sx[32 * (c + 2) + lane], t2, b0);
-        b1 = fmaf(sx[32 * (c + 3) + lane], t3, b1);
-        a0 += flip(st[32 * c + lane], (w0 << (31 - lane)) & 0x80000000u);
-        a1 += flip(st[32 * (c + 1) + lane], (w1 << (31 - lane)) & 0x80000000u);
-        a0 += flip(st[32 * (c + 2) + lane], (w2 << (31 - lane)) & 0x80000000u);
-        a1 += flip(st[32 * (c + 3) + lane], (w3 << (31 - lane)) & 0x80000000u);
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        if (c < Mw) {
+            const uint32_t w = __shfl_sync(0xffffffffu, wl, c);
+            if (c & 1) {
+                b1 = fmaf(sx[32 * c + lane], t[c], b1);
+                a1 += flip(st[32 * c + lane], (w << (31 - lane)) & 0x80000000u);
+            } else {
+                b0 = fmaf(sx[32 * c + lane], t[c], b0);
+                a0 += flip(st[32 * c + lane], (w << (31 - lane)) & 0x80000000u);
+            }
+        }
     }
-    for (; c < Mw; ++c) {
-        float t0 = __ldg(Tj + 32 * c + lane);
-        uint32_t w0 = __ldg(Bj + c);
-        b0 = fmaf(sx[32 * c + lane], t0, b0);
-        a0 += flip(st[32 * c + lane], (w0 << (31 - lane)) & 0x80000000u);
-    }
-    int d = 0;
-    for (int q = lane; q < Mw; q += 32) d += __popc(sb[q] ^ __ldg(Bj + q));
     su = warp_sum(a0 + a1);
     sv = warp_sum(b0 + b1);
     dis = warp_sum_i(d);
@@ -404,6 +404,7 @@ __global__ void k_objective(IsingView v, double *partials) {
 // seg_start[s] .. + seg_count[s]; the second node of candidate q is
 // cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
 // in shared memory once; each warp streams the rows of its candidates.
+template <int NW>
 __global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                                    const int64_t *seg_start, const int32_t *seg_count,
                                                    const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreP
         const uint32_t *Bj = v.xbits + (int64_t)gj * v.Mw;
         float su, sv;
         int dis;
-        pass0_staged(st, sx, sb, Tj, Bj, v.Mw, lane, su, sv, dis);
+        pass0_staged_all<NW>(st, sx, sb, Tj, Bj, v.Mw, lane, su, sv, dis);
         SmemRows R{st, sb, Tj, Bj, v.Mw, lane};
         float g, w;
         int passes = 0;
@@ -717,8 +718,19 @@ cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const i
                                    unsigned long long *cnt, int threads, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
     size_t smem = sizeof(float) * 2 * v.Mp + sizeof(uint32_t) * v.Mw;
-    k_score_seg<<<(unsigned)nseg, threads, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, cand,
-                                                  gid, d_out, cnt);
+    if (v.Mw > 32) return cudaErrorInvalidValue;
+#define SEG_LAUNCH(NWV)                                                                                              \
+    k_score_seg<NWV><<<(unsigned)nseg, threads, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, \
+                                                           cand, gid, d_out, cnt)
+    if (v.Mw <= 4)
+        SEG_LAUNCH(4);
+    else if (v.Mw <= 8)
+        SEG_LAUNCH(8);
+    else if (v.Mw <= 16)
+        SEG_LAUNCH(16);
+    else
+        SEG_LAUNCH(32);
+#undef SEG_LAUNCH
     note_launch();
     return cudaGetLastError();
 }
