@@ -160,6 +160,9 @@ static void free_ctx(recon_ctx *c) {
         if (b.p) cudaFree(b.p);
     free_search_bufs(c->sb);
     free_proposal(c->prop);
+    if (c->nnd_exec) cudaGraphExecDestroy(c->nnd_exec);
+    for (cudaEvent_t e : {c->nnd_ea, c->nnd_eb})
+        if (e) cudaEventDestroy(e);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     delete c;
 }

@@ -237,6 +237,11 @@ struct recon_ctx {
     uint64_t stats_calls = 0;  // best-pairs calls so far (seeds each call's random choices)
     int tuned_threads = 0;     // block width of the segmented scorer, picked by the autotuner
     int64_t graph_launches_per_iter = 0;  // kernels in one captured NNDescent iteration
+    // the captured NNDescent iteration, kept while everything it was captured
+    // with (sizes, buffers, views, parameters) stays the same
+    cudaGraphExec_t nnd_exec = nullptr;
+    std::vector<uint8_t> nnd_sig;
+    cudaEvent_t nnd_ea = nullptr, nnd_eb = nullptr;  // scoring launch inside the iteration (timing)
     std::string err;
     bool broken = false;
 

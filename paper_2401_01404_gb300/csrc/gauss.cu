@@ -217,14 +217,34 @@ __device__ __forceinline__ void gupdate_one(GaussView v, WTable W, ScoreParams p
     const float dl = w - W0;
     if (dl != 0.f) {
         const float s2i = v.s2[i], s2j = v.s2[j];
-        for (int m = lane; m < v.M; m += 32) {
-            float xi = v.xg[(int64_t)i * v.Mp + m], xj = v.xg[(int64_t)j * v.Mp + m];
-            float mi = v.mu[(int64_t)i * v.Mp + m] + dl * xj;
-            float mj = v.mu[(int64_t)j * v.Mp + m] + dl * xi;
-            v.mu[(int64_t)i * v.Mp + m] = mi;
-            v.mu[(int64_t)j * v.Mp + m] = mj;
-            v.e[(int64_t)i * v.Mp + m] = fmaf(s2i, mi, xi);
-            v.e[(int64_t)j * v.Mp + m] = fmaf(s2j, mj, xj);
+        const float *Xi = v.xg + (int64_t)i * v.Mp, *Xj = v.xg + (int64_t)j * v.Mp;
+        float *Ui = v.mu + (int64_t)i * v.Mp, *Uj = v.mu + (int64_t)j * v.Mp;
+        float *Ei = v.e + (int64_t)i * v.Mp, *Ej = v.e + (int64_t)j * v.Mp;
+        // samples in chunks of 8 per lane: every load of a chunk is in flight
+        // before the first is used (one round trip to L2 per chunk)
+        constexpr int UCH = 8;
+        for (int m0 = 0; m0 < v.M; m0 += 32 * UCH) {
+            float xa[UCH], xb[UCH], ua[UCH], ub[UCH];
+#pragma unroll
+            for (int q = 0; q < UCH; ++q) {
+                const int m = m0 + 32 * q + lane;
+                const bool ok = m < v.M;
+                xa[q] = ok ? __ldg(Xi + m) : 0.f;
+                xb[q] = ok ? __ldg(Xj + m) : 0.f;
+                ua[q] = ok ? Ui[m] : 0.f;
+                ub[q] = ok ? Uj[m] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < UCH; ++q) {
+                const int m = m0 + 32 * q + lane;
+                if (m < v.M) {
+                    const float mi = ua[q] + dl * xb[q], mj = ub[q] + dl * xa[q];
+                    Ui[m] = mi;
+                    Uj[m] = mj;
+                    Ei[m] = fmaf(s2i, mi, xa[q]);
+                    Ej[m] = fmaf(s2j, mj, xb[q]);
+                }
+            }
         }
         if (lane == 0 && !wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
     }

@@ -511,19 +511,37 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
         float *Pi = v.phi + (int64_t)i * v.Mp, *Pj = v.phi + (int64_t)j * v.Mp;
         float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
         float hi = 0.f, hj = 0.f;
-        for (int c = 0; c < v.Mw; ++c) {
-            int m = 32 * c + lane;
-            if (m >= v.M) break;
-            bool xi_neg = (Bi[c] >> lane) & 1u, xj_neg = (Bj[c] >> lane) & 1u;
-            float pi = Pi[m] + (xj_neg ? -dl : dl);
-            float pj = Pj[m] + (xi_neg ? -dl : dl);
-            float a = tanhf(pi), b = tanhf(pj);
-            Pi[m] = pi;
-            Pj[m] = pj;
-            Ti[m] = a;
-            Tj[m] = b;
-            hi += 1.f - a * a;
-            hj += 1.f - b * b;
+        // words in chunks of UCH: every load of a chunk is in flight before the
+        // first is used (one round trip to L2 per chunk, not per word)
+        constexpr int UCH = 8;
+        for (int c0 = 0; c0 < v.Mw; c0 += UCH) {
+            float pa[UCH], pb[UCH];
+            uint32_t wa[UCH], wb[UCH];
+#pragma unroll
+            for (int q = 0; q < UCH; ++q) {
+                const int c = c0 + q, m = 32 * c + lane;
+                const bool ok = c < v.Mw && m < v.M;
+                pa[q] = ok ? Pi[m] : 0.f;
+                pb[q] = ok ? Pj[m] : 0.f;
+                wa[q] = c < v.Mw ? __ldg(Bi + c) : 0u;
+                wb[q] = c < v.Mw ? __ldg(Bj + c) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < UCH; ++q) {
+                const int c = c0 + q, m = 32 * c + lane;
+                if (c < v.Mw && m < v.M) {
+                    const bool xi_neg = (wa[q] >> lane) & 1u, xj_neg = (wb[q] >> lane) & 1u;
+                    const float pi = pa[q] + (xj_neg ? -dl : dl);
+                    const float pj = pb[q] + (xi_neg ? -dl : dl);
+                    const float a = tanhf(pi), b = tanhf(pj);
+                    Pi[m] = pi;
+                    Pj[m] = pj;
+                    Ti[m] = a;
+                    Tj[m] = b;
+                    hi += 1.f - a * a;
+                    hj += 1.f - b * b;
+                }
+            }
         }
         hi = warp_sum(hi);
         hj = warp_sum(hj);

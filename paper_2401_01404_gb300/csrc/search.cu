@@ -129,7 +129,8 @@ __global__ void k_in_fill(int64_t nk, const int32_t *ids, const int64_t *inoff, 
 }
 
 // U(x) = out(x) u (at most in_cap in-neighbours, smallest random priority)
-__global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Ucap, uint64_t seed0, const int *iter,
+__global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Ucap, const unsigned long long *seed0,
+                          const int *iter,
                           const int32_t *ids,
                           const uint8_t *isnew, const int64_t *inoff, const int32_t *indeg, const int32_t *in_e,
                           int32_t *U, uint8_t *Uf, int32_t *Udeg) {
@@ -137,7 +138,7 @@ __global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Uca
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (x >= n) return;
-    const uint64_t seed = mix64(seed0 ^ (0x5bd1e995ull * (uint64_t)*iter));
+    const uint64_t seed = mix64(*seed0 ^ (0x5bd1e995ull * (uint64_t)*iter));
     int32_t *sid = sm + wib * 2 * Ucap;
     int32_t *sfl = sid + Ucap;
     const int k = klen[x];
@@ -1039,12 +1040,19 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     GROW(S.off_sd, sizeof(float) * ocap);
     GROW(S.iter, sizeof(int) * 4);
     CKS(cudaMemsetAsync(S.iter.p, 0, sizeof(int) * 4, c->stream));
+    GROW(S.seed, sizeof(unsigned long long));
+    {
+        const unsigned long long sh = seed;  // staged by the copy before the call returns
+        CKS(cudaMemcpyAsync(S.seed.p, &sh, sizeof sh, cudaMemcpyHostToDevice, c->stream));
+    }
     const int threads = c->tuned_threads ? c->tuned_threads : 256;
     const unsigned stride_grid = (unsigned)std::max(1, 8 * c->num_sms);
     cudaEvent_t ea = nullptr, eb = nullptr;
     if (c->opt.timing) {
-        CKS(cudaEventCreate(&ea));
-        CKS(cudaEventCreate(&eb));
+        if (!c->nnd_ea) CKS(cudaEventCreate(&c->nnd_ea));
+        if (!c->nnd_eb) CKS(cudaEventCreate(&c->nnd_eb));
+        ea = c->nnd_ea;
+        eb = c->nnd_eb;
     }
     // The iterations run on a private non-blocking stream (graph capture is not
     // possible on the legacy default stream), ordered after the work already on
@@ -1084,7 +1092,8 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
             const int wpb = 8;
             size_t smem = sizeof(int32_t) * 2 * Ucap * wpb;
             k_build_U<<<nblk((int64_t)n * 32, 32 * wpb), 32 * wpb, smem, gs>>>(
-                n, k, klen, in_cap, Ucap, seed, (int *)S.iter.p, (int32_t *)S.knn_id.p, (uint8_t *)S.knn_new.p,
+                n, k, klen, in_cap, Ucap, (const unsigned long long *)S.seed.p, (int *)S.iter.p, (int32_t *)S.knn_id.p,
+                (uint8_t *)S.knn_new.p,
                 (int64_t *)S.inoff.p, (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
                 (int32_t *)S.Udeg.p);
             note_launch();
@@ -1134,8 +1143,41 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
             return e;
         return cudaGetLastError();
     };
+    // everything the captured iteration depends on: a graph captured with the
+    // same values (a later search of the same shape) is replayed as it is
+    std::vector<uint8_t> sig;
+    auto put = [&](const void *p, size_t nb) {
+        const uint8_t *b = (const uint8_t *)p;
+        sig.insert(sig.end(), b, b + nb);
+    };
+    {
+        const int64_t ints[] = {n, k, in_cap, Ucap, hsize, lcap, cand_cap, ocap, (int64_t)smem_gen, warps_per_block,
+                                threads, stride_grid, c->model};
+        put(ints, sizeof ints);
+        const void *ptrs[] = {klen, gid, ea, eb, gs, c->cnt, c->cnt_host, S.knn_id.p, S.knn_d.p, S.knn_new.p,
+                              S.indeg.p, S.inoff.p, S.cursor.p, S.in_e.p, S.U.p, S.Uf.p, S.Udeg.p, S.scan_in.p,
+                              S.scan_tmp.p, S.cand.p, S.cand_d.p, S.seg_node.p, S.seg_start.p, S.seg_count.p,
+                              S.off_t.p, S.off_v.p, S.off_d.p, S.off_sv.p, S.off_sd.p, S.iter.p, S.seed.p};
+        put(ptrs, sizeof ptrs);
+        const ScoreParams sp = c->sp();
+        put(&sp, sizeof sp);
+        put(&c->W, sizeof c->W);
+        if (c->model == RECON_ISING) {
+            const IsingView v = c->iv();
+            put(&v, sizeof v);
+        } else {
+            const GaussView v = c->gv();
+            put(&v, sizeof v);
+        }
+    }
     cudaGraphExec_t exec = nullptr;
-    if (use_graph) {
+    if (use_graph && c->nnd_exec && sig == c->nnd_sig) exec = c->nnd_exec;
+    if (use_graph && !exec) {
+        if (c->nnd_exec) {
+            cudaGraphExecDestroy(c->nnd_exec);
+            c->nnd_exec = nullptr;
+            c->nnd_sig.clear();
+        }
         // a capture that fails leaves the launch-by-launch path in use
         cudaGraph_t graph = nullptr;
         const int64_t launches0 = c->stats.kernel_launches;
@@ -1154,6 +1196,9 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
         if (e != cudaSuccess) {
             exec = nullptr;
             cudaGetLastError();
+        } else {
+            c->nnd_exec = exec;
+            c->nnd_sig = std::move(sig);
         }
     }
     int it = 0;
@@ -1190,14 +1235,11 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
         }
         if ((double)delta / (double)S.klen_sum < c->opt.eps_knn) break;
     }
-    if (exec) cudaGraphExecDestroy(exec);
     if (ev_join) {
         cudaEventRecord(ev_join, gs);
         cudaStreamWaitEvent(c->stream, ev_join, 0);
         cudaEventDestroy(ev_join);
     }
-    if (ea) cudaEventDestroy(ea);
-    if (eb) cudaEventDestroy(eb);
     if (result != RECON_OK) return result;
     *iters_out = it;
     return RECON_OK;

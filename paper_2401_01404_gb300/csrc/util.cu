@@ -179,6 +179,30 @@ __global__ void __launch_bounds__(1024) k_batch_order(int64_t P, const int *batc
 // -------- scan ---------------------------------------------------------------
 constexpr int SCAN_B = 1024;
 
+constexpr int64_t SMALL_SCAN = 64 * 1024;
+
+__global__ void __launch_bounds__(SCAN_B) k_scan_small(const int64_t *in, int64_t *out, int64_t n) {
+    __shared__ int64_t s[SCAN_B];
+    const int64_t per = (n + SCAN_B - 1) / SCAN_B;
+    const int64_t b = threadIdx.x * per, e = min(n, b + per);
+    int64_t sum = 0;
+    for (int64_t q = b; q < e; ++q) sum += in[q];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < SCAN_B; o <<= 1) {
+        int64_t add = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int64_t run = s[threadIdx.x] - sum;  // exclusive prefix of this thread's run
+    for (int64_t q = b; q < e; ++q) {
+        const int64_t v = in[q];
+        out[q] = run;
+        run += v;
+    }
+}
+
 __global__ void k_scan_block(const int64_t *in, int64_t *out, int64_t n, int64_t *sums) {
     __shared__ int64_t s[SCAN_B];
     int64_t g = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
@@ -331,9 +355,16 @@ int64_t scan_tmp_elems(int64_t n) {
     return total + 2;
 }
 
-// exclusive scan, recursive over block sums
+// exclusive scan, recursive over block sums; up to SMALL_SCAN elements in one
+// block (each thread scans a contiguous run, the runs' sums are scanned in
+// shared memory), which saves the recursion's launches on the many short scans
+// of a search
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    if (n > SCAN_B && n <= SMALL_SCAN) {
+        k_scan_small<<<1, SCAN_B, 0, s>>>(in, out, n); note_launch();
+        return cudaGetLastError();
+    }
     int64_t nb = (n + SCAN_B - 1) / SCAN_B;
     if (nb == 1) {
         k_scan_block<<<1, SCAN_B, 0, s>>>(in, out, n, nullptr); note_launch();
