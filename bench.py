@@ -104,18 +104,34 @@ class Clocks:
 
 # ------------------------------------------------------------------ workload
 
-def _workload(name, rank, device):
+def _workload(name, rank, device, N=None, M=None, sweeps=None):
+    """The named workload; rank r > 0 gets an independent replica (a new draw
+    of the same planted model, same sizes and penalty).  N, M, sweeps shrink it
+    (tests)."""
     from paper_2401_01404_gb300 import inputs
 
-    wl = inputs.config(name, device=device)
+    wl = inputs.config(name, device=device, N=N, M=M, sweeps=sweeps)
     if rank:
-        # independent replica per rank: a new sample draw of the same planted model
         lam = wl.lam
         wl = inputs.ising_workload(name, wl.N, wl.M, "regular" if "n2000" in name else "er",
                                    4 if "n2000" in name else 5, "pm" if "n2000" in name else "normal",
-                                   0.3, 0.0, 1000, 2000 + 7919 * rank, wl.k, wl.kappa, device)
+                                   0.3, 0.0, sweeps or 1000, 2000 + 7919 * rank, wl.k, wl.kappa, device)
         wl.lam = lam
     return wl
+
+
+def _reduce_over_ranks(t_local, units_local, device):
+    """Whole-job figures: the slowest rank's time and the units of all ranks."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_local, units_local
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    uu = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return tt.item(), uu.item()
 
 
 def _cpu_baseline(wl, lam, seconds):
@@ -379,13 +395,7 @@ def run_ours(a):
     obj = ctx.objective()
     ctx.close()
 
-    t_max, units = t_local, units_local
-    if world > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        uu = torch.tensor([units_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(uu, op=dist.ReduceOp.SUM)
-        t_max, units = tt.item(), uu.item()
+    t_max, units = _reduce_over_ranks(t_local, units_local, "cuda")
 
     # end to end: init from pinned host samples, one step, model back to the host
     e2e_steps = max(1, min(a.steps, 5))
@@ -402,6 +412,7 @@ def run_ours(a):
         c2.close()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    t_e2e, e2e_units = _reduce_over_ranks(t_e2e, e2e_units, "cuda")
 
     if rank != 0:
         if world > 1:
