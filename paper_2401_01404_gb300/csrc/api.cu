@@ -14,6 +14,17 @@
 static thread_local std::string g_err;  // errors without a context
 thread_local recon_ctx *tl_ctx = nullptr;
 
+cudaError_t recon_malloc(void **p, size_t bytes) {
+    recon_ctx *c = tl_ctx;
+    if (c && c->alloc_limit && c->alloc_total + bytes > c->alloc_limit) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess && c) c->alloc_total += bytes;
+    return e;
+}
+
 recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -57,7 +68,7 @@ bool ensure_buf(recon_ctx *c, int slot, size_t bytes) {
     }
     size_t want = std::max<size_t>(bytes, 256);
     want += want / 4;
-    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    if (recon_malloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
         set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", want);
         return false;
@@ -102,8 +113,8 @@ static recon_status read_err_flags(recon_ctx *c, unsigned long long *flags) {
 
 static recon_status alloc_table(recon_ctx *c, uint64_t cap) {
     WTable T{};
-    if (cudaMalloc(&T.keys, sizeof(unsigned long long) * cap) != cudaSuccess ||
-        cudaMalloc(&T.vals, sizeof(float) * cap) != cudaSuccess) {
+    if (recon_malloc((void **)&T.keys, sizeof(unsigned long long) * cap) != cudaSuccess ||
+        recon_malloc((void **)&T.vals, sizeof(float) * cap) != cudaSuccess) {
         cudaGetLastError();
         if (T.keys) cudaFree(T.keys);
         return set_err(c, RECON_ENOMEM, "coupling table of %llu slots", (unsigned long long)cap);
@@ -168,7 +179,7 @@ static void free_ctx(recon_ctx *c) {
 }
 
 static recon_status alloc_dev(recon_ctx *c, void **p, size_t bytes) {
-    if (cudaMalloc(p, std::max<size_t>(bytes, 4)) != cudaSuccess) {
+    if (recon_malloc(p, std::max<size_t>(bytes, 4)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", bytes);
@@ -276,6 +287,8 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     }
     recon_ctx *c = new recon_ctx();
     c->bufs.resize(BUF_NSLOTS);
+    if (const char *lim = getenv("RECON_FAULT_ALLOC_LIMIT")) c->alloc_limit = strtoull(lim, nullptr, 10);
+    if (const char *st = getenv("RECON_FAULT_SCREEN_STALL")) c->fault_screen_stall = atoi(st) != 0;
     c->model = model;
     c->device = dev;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);

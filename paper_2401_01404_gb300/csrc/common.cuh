@@ -258,6 +258,11 @@ struct recon_ctx {
     }
     GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
     bool force_exact = false;  // exact gains even in gradient-distance mode (proposal targets)
+    // host-side fault injection (tests): a cap on the device bytes the context
+    // may request (RECON_FAULT_ALLOC_LIMIT), and a screen whose loads are never
+    // issued, so that its bounded waits run out (RECON_FAULT_SCREEN_STALL)
+    uint64_t alloc_limit = 0, alloc_total = 0;
+    bool fault_screen_stall = false;
     ScoreParams sp() const {
         return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp,
                            opt.distance == RECON_DIST_GRADIENT && !force_exact ? 1 : 0};
@@ -266,6 +271,8 @@ struct recon_ctx {
 
 // the context whose API call is running on this thread (for launch counting)
 extern thread_local recon_ctx *tl_ctx;
+// cudaMalloc under the current context's allocation cap (if one is set)
+cudaError_t recon_malloc(void **p, size_t bytes);
 inline void note_launch() {
     if (tl_ctx) tl_ctx->stats.kernel_launches++;
 }

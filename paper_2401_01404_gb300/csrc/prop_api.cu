@@ -150,7 +150,7 @@ cudaError_t grow(DBuf &b, size_t bytes, cudaStream_t st) {
         b.p = nullptr;
         b.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, bytes + bytes / 4);
+    cudaError_t e = recon_malloc(&b.p, bytes + bytes / 4);
     if (e == cudaSuccess) b.bytes = bytes + bytes / 4;
     return e;
 }

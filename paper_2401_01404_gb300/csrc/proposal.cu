@@ -231,7 +231,7 @@ static cudaError_t ensure(DBuf &b, size_t bytes, cudaStream_t st) {
         b.p = nullptr;
         b.bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&b.p, bytes);
+    cudaError_t e = recon_malloc(&b.p, bytes);
     if (e == cudaSuccess) b.bytes = bytes;
     return e;
 }

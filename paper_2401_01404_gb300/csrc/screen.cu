@@ -222,6 +222,7 @@ struct ScreenArgs {
     int64_t cap;
     unsigned long long *count;
     unsigned long long *err;
+    int stall;          // fault injection: issue no loads, so the bounded waits run out
 };
 
 __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         if (lane == 0) {  // TMA producer
             UnitWalker walk(a.T);
             int64_t kb_all = 0;
-            for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x) {
+            for (int64_t t = blockIdx.x; t < a.ntiles && !a.stall && !*(volatile int *)abort; t += gridDim.x) {
                 int ra, rb;
                 walk.map(t, ra, rb);
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
@@ -561,6 +562,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.cap = cap;
     a.count = count;
     a.err = c->cnt;
+    a.stall = c->fault_screen_stall ? 1 : 0;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);
     k_screen<<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();

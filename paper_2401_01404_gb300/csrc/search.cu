@@ -665,7 +665,7 @@ static bool grow(recon_ctx *c, DBuf &b, size_t bytes) {
     }
     size_t want = std::max<size_t>(bytes, 256);
     want = want + want / 4;
-    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    if (recon_malloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
         set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", want);
         return false;
@@ -679,7 +679,7 @@ static bool grow_keep(recon_ctx *c, DBuf &b, size_t bytes, size_t keep) {
     size_t want = std::max<size_t>(bytes, 256);
     want = want + want / 2;
     void *p = nullptr;
-    if (cudaMalloc(&p, want) != cudaSuccess) {
+    if (recon_malloc(&p, want) != cudaSuccess) {
         cudaGetLastError();
         set_err(c, RECON_ENOMEM, "device allocation of %zu bytes failed", want);
         return false;
