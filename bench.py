@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--scale-caps", type=int, default=8)
     ap.add_argument("--screen-bench", type=int, nargs=2, metavar=("N", "M"), default=None,
                     help="time only the tensor-core screen on N nodes x M seeded random spins")
+    ap.add_argument("--screen-fp8", action="store_true",
+                    help="E4M3 screen operands (Ising; exact, wider margin) for --screen-bench and the scale leg")
     ap.add_argument("--findbest-scaling", type=int, nargs="*", metavar="N", default=None,
                     help="FindBest runtime against N on the paper's synthetic Gaussian (M = 10)")
     ap.add_argument("--convergence", type=int, nargs="*", metavar="N", default=None,
@@ -250,7 +252,7 @@ def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
     return out
 
 
-def _scale_recall(R, name, stream, rows_n, max_cap):
+def _scale_recall(R, name, stream, rows_n, max_cap, fp8=False):
     """Time to 0.99 best-pair recall on a workload too large for an exhaustive
     ground truth.  Truth: a seeded subsample S of nodes, every pair incident to
     S scored against all N columns (recon_row_best); recall = found best pairs
@@ -307,6 +309,22 @@ def _scale_recall(R, name, stream, rows_n, max_cap):
 
     out["chosen_recall"] = recall(p_scr)
     scr.close()
+    if fp8:
+        # the same exact screen on E4M3 operands (twice the tensor rate, wider margin)
+        s8 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1,
+                     screen_fp8=1)
+        s8.best_pairs(k, kappa)
+        s0 = s8.stats()
+        (p8, d8), t8 = timed(lambda: s8.best_pairs(k, kappa))
+        s1 = s8.stats()
+        dflop, dms = s1["screen_flop"] - s0["screen_flop"], s1["screen_ms"] - s0["screen_ms"]
+        out["chosen_fp8_s"] = t8
+        out["screen_fp8"] = {"tflops": dflop / (dms / 1e3) / 1e12 if dms else None, "ms": dms,
+                             "survivors": s1["screen_survivors"] - s0["screen_survivors"],
+                             "same_best_pairs": bool(np.array_equal(d8, d_scr) and
+                                                     {tuple(x) for x in p8.tolist()} ==
+                                                     {tuple(x) for x in p_scr.tolist()})}
+        s8.close()
     # learned proposal: pretrained on a 10^5-node draw of the same planted model
     t = time.perf_counter()
     pre = inputs.ising_workload(name + "_pretrain", 100000, M, "er", 5, "normal", 0.3, 0.0, 300, 4243, k, kappa, "cuda")
@@ -464,7 +482,8 @@ def run_ours(a):
                                          "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
         line["time_to_recall"] = ttr
     if a.scale_workload and rank == 0:
-        line["time_to_recall_scale"] = _scale_recall(R, a.scale_workload, stream, a.scale_rows, a.scale_caps)
+        line["time_to_recall_scale"] = _scale_recall(R, a.scale_workload, stream, a.scale_rows, a.scale_caps,
+                                                     a.screen_fp8)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -550,7 +569,8 @@ def run_screen_bench(a):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(int(inputs.rng(N + M, inputs.SAMPLES).integers(1 << 62)))
     X = (torch.randint(0, 2, (M, N), generator=gen, device="cuda", dtype=torch.int8) * 2 - 1).contiguous()
-    ctx = R.Recon(X, R.RECON_ISING, lam=inputs.default_lambda(N, M, 2.0), knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    ctx = R.Recon(X, R.RECON_ISING, lam=inputs.default_lambda(N, M, 2.0), knn_mode=R.RECON_KNN_SCREEN, timing=1,
+                  screen_fp8=int(a.screen_fp8))
     for _ in range(max(a.warmup, 1)):
         ctx.best_pairs(16, 1.0)
     s0 = ctx.stats()
@@ -561,9 +581,10 @@ def run_screen_bench(a):
     ms = (s1["screen_ms"] - s0["screen_ms"]) / a.steps
     tf = (s1["screen_flop"] - s0["screen_flop"]) / a.steps / (ms / 1e3) / 1e12
     peaks = _peaks()
-    bf16 = peaks.get("bf16_tflops", 1900.0)
-    print(json.dumps({"kernel": "k_screen", "N": N, "M": M, "steps": a.steps, "ms_per_launch": ms, "tflops": tf,
-                      "peak": bf16, "frac": tf / bf16,
+    # fp8 peak: the measured bf16 peak times the nominal fp8/bf16 ratio (4.5 / 2.25)
+    peak = peaks.get("bf16_tflops", 1900.0) * (2.0 if a.screen_fp8 else 1.0)
+    print(json.dumps({"kernel": "k_screen", "operands": "e4m3" if a.screen_fp8 else "bf16", "N": N, "M": M,
+                      "steps": a.steps, "ms_per_launch": ms, "tflops": tf, "peak": peak, "frac": tf / peak,
                       "survivors_per_launch": (s1["screen_survivors"] - s0["screen_survivors"]) / a.steps,
                       "data": "seeded uniform random spins"}), flush=True)
 

@@ -270,6 +270,8 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
         return set_err(nullptr, RECON_EINVAL, "unknown distance");
     if (o.distance == RECON_DIST_GRADIENT && o.knn_mode == RECON_KNN_SCREEN)
         return set_err(nullptr, RECON_EUNSUPPORTED, "the gradient distance ranks pairs the screen does not keep");
+    if (o.screen_fp8 && model != RECON_ISING)
+        return set_err(nullptr, RECON_EUNSUPPORTED, "fp8 screen operands are for the Ising model only");
     if (!(o.learned_frac >= 0.f && o.learned_frac <= 1.f))
         return set_err(nullptr, RECON_EINVAL, "learned_frac outside [0, 1]");
     if (o.seed_mode != RECON_SEED_RANDOM && o.seed_mode != RECON_SEED_LEARNED)

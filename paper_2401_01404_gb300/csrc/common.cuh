@@ -365,15 +365,20 @@ cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned lo
                            bool *result_in_alt, cudaStream_t s);
 
 // screen.cu
-cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1);
-float screen_rel_err(int model, int Mp);
+// operands: bf16 rows of K = 2 Mp, or (Ising, fp8) E4M3 rows padded to a multiple of 128
+int screen_k(recon_ctx *c, bool fp8);
+cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1, bool fp8);
+float screen_rel_err(int model, int Mp, bool fp8);
+float screen_abs_err_fp8(int64_t M);
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
-                          unsigned long long *count, float margin_scale, double *flop_out);
-// general form: operands of K columns (a multiple of 64), threshold `thr` on |G_ij|,
-// margin rel * (l_i + l_j) (or l_i l_j) when l1 is given, stored couplings skipped when skip_stored
+                          unsigned long long *count, float margin_scale, double *flop_out, bool fp8);
+// general form: operands of K columns (a multiple of 64 bf16 or 128 fp8), of which the first
+// k_valid are nonzero; threshold `thr` on |G_ij|, margin rel * (l_i + l_j) (or l_i l_j) + abs_margin
+// when l1 is given, stored couplings skipped when skip_stored
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
-                             unsigned long long *count, double *flop_out);
+                             unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
+                             int k_valid);
 
 // host helpers (api.cu)
 recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...);

@@ -29,6 +29,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -39,8 +40,9 @@ namespace {
 // a unit of work is a 128 x 256 block of G: rows BM from A, columns BN from B;
 // units are the two 128-row halves of the 256 x 256 super-tiles (SUP) of the
 // upper triangle
-constexpr int BM = 128, BN = 256, SUP = 256, BK = 64, STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+// BK: elements of a 128-byte k-block row: 64 in bf16, 128 in fp8
+constexpr int BM = 128, BN = 256, SUP = 256, BK = 64, BK8 = 128, STAGES = 4;
+constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
 constexpr uint32_t TMEM_COLS = 512;  // two accumulators of 256 f32 columns
 constexpr int THREADS = 192;
 
@@ -103,6 +105,12 @@ __device__ __forceinline__ uint64_t desc_sw128(const void *p) {
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// FP8 (E4M3 x E4M3) operands, K = 32 per instruction, FP32 accumulation
+__device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
@@ -211,9 +219,11 @@ struct ScreenArgs {
     int n;              // nodes
     int T;              // super-tiles per side
     int64_t ntiles;     // units: 2 T (T + 1) / 2
-    int nk;             // K / BK
+    int nk;             // K / BK (K / BK8 for fp8)
+    int last_mma;       // MMAs issued for the last k-block (trailing zero padding skipped)
     float lambda;
     float rel_err;      // margin per unit of the per-node norms
+    float abs_margin;   // plus this much (fp8: the subnormal rounding of the residuals)
     int product_margin; // margin rel_err * l_i * l_j (Gaussian) instead of rel_err * (l_i + l_j)
     const float *l1;    // per-node norms of the margin
     WTable W;           // pairs with a stored coupling are left to the caller
@@ -225,6 +235,7 @@ struct ScreenArgs {
     int stall;          // fault injection: issue no loads, so the bounded waits run out
 };
 
+template <bool F8>
 __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
                                                        const __grid_constant__ CUtensorMap tB, ScreenArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -271,8 +282,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     const int s = (int)(kb_all % STAGES);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
                     mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-                    tma_2d(sA + s * A_BYTES, &tA, kb * BK, ra, full + s);
-                    tma_2d(sB + s * B_BYTES, &tB, kb * BK, rb, full + s);
+                    tma_2d(sA + s * A_BYTES, &tA, kb * (F8 ? BK8 : BK), ra, full + s);
+                    tma_2d(sB + s * B_BYTES, &tB, kb * (F8 ? BK8 : BK), rb, full + s);
                 }
             }
             // let every copy issued above land before the CTA can leave
@@ -287,7 +298,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         }
     } else if (warp == 5) {
         if (lane == 0) {  // MMA issuer
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+            // F32 accumulator; A and B bf16 (kind::f16: type 1) or E4M3 (kind::f8f6f4: type 0)
+            const uint32_t ab = F8 ? 0u : 1u;
+            const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
             int64_t kb_all = 0, it = 0;
             for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x, ++it) {
@@ -304,8 +317,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     }
                     tc_fence_after();
                     const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * B_BYTES);
+                    // four MMAs per 128-byte k-block row (K = 16 bf16 or 32 fp8 each, 32 bytes
+                    // apart: +2 in the descriptor's 16-byte address units)
+                    const int nm = kb + 1 == a.nk ? a.last_mma : 4;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                    for (int k = 0; k < 4; ++k) {
+                        if (k >= nm) break;
+                        if constexpr (F8)
+                            mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        else
+                            mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                    }
                     mma_commit(empty + s);
                 }
                 mma_commit(acc_full + b);
@@ -354,7 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             //   product margin rel l_i l_j:      c_j = l_j,     s = rel l_i,  thr = lambda
             const float li = li_n;
             const float sc = a.product_margin ? a.rel_err * li : 1.f;
-            const float thr = a.product_margin ? a.lambda : a.lambda - a.rel_err * li;
+            const float thr = (a.product_margin ? a.lambda : a.lambda - a.rel_err * li) - a.abs_margin;
             const float f = a.product_margin ? 1.f : a.rel_err;
             const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
             const float4 c1 = make_float4(f * n1.x, f * n1.y, f * n1.z, f * n1.w);
@@ -488,14 +510,53 @@ __global__ void k_prep_gauss(GaussView v, __nv_bfloat16 *A, __nv_bfloat16 *B, fl
     if (lane == 0) l1[i] = sqrtf(se) + sqrtf(sx);  // |e|_2 + |x|_2, combined with the partner's by the margin
 }
 
+// Ising operands in FP8 E4M3 (uint8 codes): the same rows, each padded with
+// zeros to K8 = a multiple of 128 entries; spins are exact, residuals rounded
+// to nearest (saturating, |r| < 2 anyway)
+__global__ void k_prep_ising_fp8(IsingView v, int K8, uint8_t *A, uint8_t *B, float *l1) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    float s = 0.f;
+    for (int m = 2 * v.Mp + lane; m < K8; m += 32) {
+        A[i * K8 + m] = 0;
+        B[i * K8 + m] = 0;
+    }
+    for (int m = lane; m < v.Mp; m += 32) {
+        const float x = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? -1.f : 1.f;
+        const float r = m < v.M ? x - v.t[i * v.Mp + m] : 0.f;
+        const uint8_t rb = (uint8_t)__nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3);
+        const uint8_t xb = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+        A[i * K8 + m] = rb;
+        A[i * K8 + v.Mp + m] = xb;
+        B[i * K8 + m] = xb;
+        B[i * K8 + v.Mp + m] = rb;
+        s += fabsf(r);
+    }
+    s = warp_sum(s);
+    if (lane == 0) l1[i] = s;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
-// bf16 operand rows of K = 2 Mp entries; survivors of the screen into out
-cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1) {
+// operand row length: 2 Mp bf16 entries, or 2 Mp fp8 entries padded to 128
+int screen_k(recon_ctx *c, bool fp8) {
+    const int k = 2 * (int)c->Mp;
+    return fp8 ? (k + BK8 - 1) / BK8 * BK8 : k;
+}
+
+// bf16 (or, for the Ising model, fp8) operand rows and the margin's norms
+cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1, bool fp8) {
     const int64_t warps = c->N;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+    if (fp8) {
+        if (c->model != RECON_ISING) return cudaErrorInvalidValue;
+        k_prep_ising_fp8<<<grid, 256, 0, c->stream>>>(c->iv(), screen_k(c, true), (uint8_t *)A, (uint8_t *)B, l1);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (c->model == RECON_ISING)
         k_prep_ising<<<grid, 256, 0, c->stream>>>(c->iv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, l1);
     else
@@ -512,16 +573,27 @@ cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1) {
 // Gaussian: both operands are rounded, |dg_ij| <= (2u + u^2) sum_m (|e_i x_j| + |x_i e_j|)
 //   <= (2u + u^2)(|e_i|_2 |x_j|_2 + |x_i|_2 |e_j|_2) <= (2u + u^2) l_i l_j with
 //   l = |e|_2 + |x|_2 (Cauchy-Schwarz), plus the accumulation error.
-float screen_rel_err(int model, int Mp) {
+float screen_rel_err(int model, int Mp, bool fp8) {
     const double u = 1.0 / 256.0, acc = 2.0 * Mp * 1.2e-7;
+    // E4M3: 3 stored mantissa bits, |dr| <= 2^-4 |r| + ...; the products are
+    // exact, and the accumulation is charged 2^-12 of the running magnitude per
+    // MMA (K = 32), which also covers an accumulator narrower than FP32
+    if (fp8) return (float)(1.0 / 16.0 + (2.0 * Mp / 32.0 + 1.0) / 4096.0);
     if (model == RECON_ISING) return (float)(u + acc);
     return (float)(2 * u + u * u + acc);
 }
 
+// ... + 2^-10 per residual below the smallest normal (2^-6, subnormal spacing
+// 2^-9): sum_m (|dr_i| + |dr_j|) gains at most 2 M 2^-10
+float screen_abs_err_fp8(int64_t M) { return (float)(2.0 * (double)M / 1024.0); }
+
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
-                             unsigned long long *count, double *flop_out) {
-    if (K % BK) return cudaErrorInvalidValue;
+                             unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
+                             int k_valid) {
+    const int bke = fp8 ? BK8 : BK;  // elements per 128-byte k-block row
+    const int kchunk = fp8 ? 32 : 16;  // elements per MMA
+    if (K % bke || k_valid <= K - bke || k_valid > K || k_valid % kchunk) return cudaErrorInvalidValue;
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&g_encode, 12000,
@@ -530,30 +602,34 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     }
     CUtensorMap ta, tb;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
-    cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    cuuint32_t box_a[2] = {BK, BM}, box_b[2] = {BK, BN};
+    const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint64_t strides[1] = {(cuuint64_t)K * (fp8 ? 1 : 2)};
+    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN};
     cuuint32_t es[2] = {1, 1};
-    if (g_encode(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(A), dims, strides, box_a, es,
+    if (g_encode(&ta, dt, 2, const_cast<void *>(A), dims, strides, box_a, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        g_encode(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), dims, strides, box_b, es,
+        g_encode(&tb, dt, 2, const_cast<void *>(B), dims, strides, box_b, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + 4 * BN * sizeof(float);
-    static int attr_device = -1;  // the attribute is per device; set it once for each
-    if (attr_device != c->device) {
-        cudaError_t e = cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int attr_device[2] = {-1, -1};  // per device and variant; set once for each
+    if (attr_device[fp8] != c->device) {
+        cudaError_t e = fp8 ? cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_device = c->device;
+        attr_device[fp8] = c->device;
     }
     ScreenArgs a;
     a.n = (int)c->N;
     a.T = (int)((c->N + SUP - 1) / SUP);
     a.ntiles = (int64_t)a.T * (a.T + 1);  // two units per super-tile
-    a.nk = K / BK;
+    a.nk = K / bke;
+    a.last_mma = (k_valid - (a.nk - 1) * bke) / kchunk;
     a.lambda = thr;
     a.rel_err = rel;
+    a.abs_margin = abs_margin;
     a.product_margin = product_margin;
     a.l1 = l1;
     a.W = c->W;
@@ -564,14 +640,18 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);
-    k_screen<<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    if (fp8)
+        k_screen<true><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    else
+        k_screen<false><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();
-    if (flop_out) *flop_out = 2.0 * BM * BN * (double)K * (double)a.ntiles;
+    if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.ntiles;
     return cudaGetLastError();
 }
 
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
-                          unsigned long long *count, float margin_scale, double *flop_out) {
-    return launch_screen_ex(c, A, B, 2 * (int)c->Mp, (float)c->opt.lambda, l1, margin_scale,
-                            c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out);
+                          unsigned long long *count, float margin_scale, double *flop_out, bool fp8) {
+    return launch_screen_ex(c, A, B, screen_k(c, fp8), (float)c->opt.lambda, l1, margin_scale,
+                            c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out, fp8,
+                            fp8 ? screen_abs_err_fp8(c->M) : 0.f, 2 * (int)c->Mp);
 }

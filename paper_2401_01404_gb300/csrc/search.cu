@@ -1444,11 +1444,13 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
     SearchBufs &S = SB(c);
     S.res_n = 0;
     S.g0_K = 0;
-    const int64_t N = c->N, K = 2 * c->Mp;
-    GROW(S.scr_A, sizeof(uint16_t) * (size_t)N * K);
-    GROW(S.scr_B, sizeof(uint16_t) * (size_t)N * K);
+    const bool fp8 = c->opt.screen_fp8 != 0;
+    const int64_t N = c->N, K = screen_k(c, fp8);
+    const size_t esz = fp8 ? 1 : sizeof(uint16_t);
+    GROW(S.scr_A, esz * (size_t)N * K);
+    GROW(S.scr_B, esz * (size_t)N * K);
     GROW(S.scr_l1, sizeof(float) * N);
-    CKS(launch_screen_prep(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p));
+    CKS(launch_screen_prep(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, fp8));
     int64_t nnz = 0;
     {
         CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
@@ -1459,7 +1461,7 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
         nnz = (int64_t)v;
     }
     int64_t cap = std::max<int64_t>(int64_t(1) << 20, 16 * m);
-    const float rel = screen_rel_err(c->model, (int)c->Mp);
+    const float rel = screen_rel_err(c->model, (int)c->Mp, fp8);
     unsigned long long nsurv = 0;
     for (int attempt = 0; attempt < 3; ++attempt) {
         GROW(S.cand, sizeof(int32_t) * 2 * (cap + nnz + 1));
@@ -1477,7 +1479,7 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
         }
         double flop = 0.0;
         CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
-                          counter(c, CNT_SCRATCH1), rel, &flop));
+                          counter(c, CNT_SCRATCH1), rel, &flop, fp8));
         if (c->opt.timing) {
             CKS(cudaEventRecord(eb, c->stream));
             c->timed.push_back({ea, eb, -1});

@@ -30,7 +30,8 @@ class recon_options(C.Structure):
                 ("max_knn_iters", C.c_int32), ("w_clamp", C.c_float), ("h_clamp", C.c_float),
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
                 ("timing", C.c_int32), ("no_graphs", C.c_int32),
-                ("learned_frac", C.c_float), ("distance", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("learned_frac", C.c_float), ("distance", C.c_int32), ("screen_fp8", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class recon_stats(C.Structure):

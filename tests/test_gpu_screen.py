@@ -2,7 +2,8 @@
 the exact best pairs — the screen only discards pairs whose gain is provably
 zero, and the survivors are scored exactly.  Checked against the oracle and
 against the CUDA-core exhaustive search, element by element, on sizes with
-ragged tiles (N not a multiple of 128, M not a multiple of 64)."""
+ragged tiles (N not a multiple of 128, M not a multiple of 64).  The same
+for the FP8 (E4M3) operands, whose wider margin keeps the result exact."""
 import math
 
 import numpy as np
@@ -41,15 +42,17 @@ def _close(g_gpu, g_ref):
     return np.abs(np.asarray(g_gpu, dtype=np.float64) - g_ref) <= tol
 
 
+@pytest.mark.parametrize("fp8", [0, 1])
 @pytest.mark.parametrize("N,M,c", [(100, 200, 1.0), (300, 130, 0.5), (257, 1000, 1.0), (129, 37, 0.7)])
-def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c):
+def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c, fp8):
     X = _wl(N, M, 100 + N)
     lam = inputs.default_lambda(N, M, c)
     o = oracle.IsingOracle(X, lam)
     allp = oracle.all_pairs(np.arange(N))
     g_ref, _ = o.score(allp)
     npos = int((g_ref > 1e-6 * g_ref.max()).sum())
-    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1,
+                  screen_fp8=fp8)
     kappa = (len(allp) + 0.4) / N  # ask for every pair: the screen returns exactly its survivors
     p, d = scr.best_pairs(4, kappa)
     found = {tuple(x) for x in p.tolist()}
@@ -57,17 +60,19 @@ def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c):
     assert pos <= found, len(pos - found)
     st = scr.stats()
     assert st["screen_launches"] == 1 and st["screen_survivors"] == len(p)
-    assert len(p) < len(allp) or npos > len(allp) // 2  # the screen discarded pairs
+    if not fp8:
+        assert len(p) < len(allp) or npos > len(allp) // 2  # the screen discarded pairs
     gd = dict(zip(map(tuple, allp.tolist()), g_ref))
     assert _close(-d, np.array([gd[x] for x in map(tuple, p.tolist())])).all()
 
 
+@pytest.mark.parametrize("fp8", [0, 1])
 @pytest.mark.parametrize("N,M,kappa", [(200, 300, 1.0), (500, 500, 2.0), (1100, 250, 1.0)])
-def test_screen_best_equals_exhaustive(R, N, M, kappa):
+def test_screen_best_equals_exhaustive(R, N, M, kappa, fp8):
     X = _wl(N, M, 200 + N)
     lam = inputs.default_lambda(N, M)
     Xs = np.ascontiguousarray(X.T)
-    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
     ex = R.Recon(Xs, R.RECON_ISING, lam=lam)
     m = int(math.floor(kappa * N + 0.5))
     p1, d1 = scr.best_pairs(8, kappa)
@@ -111,3 +116,32 @@ def test_screen_gaussian(R, oracle):
     found = {tuple(x) for x in p.tolist()}
     pos = {tuple(x) for x, g in zip(allp.tolist(), g_ref) if g > 1e-6 * g_ref.max()}
     assert pos <= found
+
+
+def test_fp8_screen_matches_bf16_on_a_larger_lattice(R):
+    """Several hundred tiles, M = 200 (K = 448: the fp8 rows end in a half
+    k-block): both operand types give the same best pairs, and the fp8 margin
+    only adds survivors."""
+    N, M = 6000, 200
+    edges = inputs.erdos_renyi(N, 3, inputs.rng(7, inputs.GRAPH))
+    w = inputs.rng(7, inputs.COUPLINGS).normal(0, 0.5, len(edges))
+    X = inputs.gibbs_ising(N, edges, w, np.zeros(N), M, 100, 7)
+    Xs = np.ascontiguousarray(X.T)
+    lam = inputs.default_lambda(N, M)
+    out = []
+    for fp8 in (0, 1):
+        c = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
+        p, d = c.best_pairs(16, 1.0)
+        out.append((p, d, c.stats()["screen_survivors"]))
+        c.close()
+    (p0, d0, s0), (p1, d1, s1) = out
+    assert s1 >= s0
+    assert np.array_equal(d0, d1)
+    assert {tuple(x) for x in p0.tolist()} == {tuple(x) for x in p1.tolist()}
+
+
+def test_fp8_screen_is_refused_for_the_gaussian_model(R):
+    X = np.ones((20, 6), dtype=np.float32)
+    with pytest.raises(R.ReconError) as e:
+        R.Recon(X, R.RECON_GAUSSIAN, lam=1.0, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=1)
+    assert e.value.status == R.RECON_EUNSUPPORTED
