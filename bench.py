@@ -574,9 +574,12 @@ def run_screen_bench(a):
     for _ in range(max(a.warmup, 1)):
         ctx.best_pairs(16, 1.0)
     s0 = ctx.stats()
+    clocks = Clocks(torch.cuda.current_device())
+    time.sleep(0.3)
     for _ in range(a.steps):
         ctx.best_pairs(16, 1.0)
     torch.cuda.synchronize()
+    ck = clocks.stop()
     s1 = ctx.stats()
     ms = (s1["screen_ms"] - s0["screen_ms"]) / a.steps
     tf = (s1["screen_flop"] - s0["screen_flop"]) / a.steps / (ms / 1e3) / 1e12
@@ -586,7 +589,7 @@ def run_screen_bench(a):
     print(json.dumps({"kernel": "k_screen", "operands": "e4m3" if a.screen_fp8 else "bf16", "N": N, "M": M,
                       "steps": a.steps, "ms_per_launch": ms, "tflops": tf, "peak": peak, "frac": tf / peak,
                       "survivors_per_launch": (s1["screen_survivors"] - s0["screen_survivors"]) / a.steps,
-                      "data": "seeded uniform random spins"}), flush=True)
+                      "clocks": ck, "data": "seeded uniform random spins"}), flush=True)
 
 
 def _paper_gaussian(N, M, seed):

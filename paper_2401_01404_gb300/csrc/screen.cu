@@ -44,7 +44,11 @@ namespace {
 constexpr int BM = 128, BN = 256, SUP = 256, BK = 64, BK8 = 128, STAGES = 4;
 constexpr int A_BYTES = BM * 128, B_BYTES = BN * 128;
 constexpr uint32_t TMEM_COLS = 512;  // two accumulators of 256 f32 columns
-constexpr int THREADS = 192;
+// warps 0-7: epilogue (row group w % 4, column half w / 4); 8: TMA producer; 9: MMA issuer
+constexpr int EPI_WARPS = 8, PRODUCER_WARP = 8, MMA_WARP = 9, THREADS = 32 * (EPI_WARPS + 2);
+// survivors are staged per epilogue warp in shared memory and written out in
+// batches: one atomic reservation and one round of stored-coupling lookups per batch
+constexpr int SBUF = 128;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -90,6 +94,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile in
         }
     }
 }
+// the same box into the same shared-memory offset of every CTA in `mask`, each
+// copy signalling the mbarrier at the same offset in its CTA
+__device__ __forceinline__ void tma_2d_mc(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar,
+                                          uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -115,6 +137,14 @@ __device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+// one arrival, once the MMAs issued so far are done, on the mbarrier at this
+// offset in every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     su32(bar)),
+                 "h"(mask)
                  : "memory");
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -248,20 +278,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     int *abort = (int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // CTA pairs (clusters of 2) take the two halves of one super-tile: they share
+    // its B rows, each loading one 128-row half and multicasting it to both
+    const uint32_t rank = cluster_rank();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(empty + s, 1);
+            mbar_init(empty + s, 2);  // a stage is free once both CTAs' MMAs have read it
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full + b, 1);
-            mbar_init(acc_empty + b, 4);  // one arrival per epilogue warp
+            mbar_init(acc_empty + b, EPI_WARPS);  // one arrival per epilogue warp
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 5) {
+    if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                      "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -269,9 +302,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
+    if (warp == PRODUCER_WARP) {
         if (lane == 0) {  // TMA producer
             UnitWalker walk(a.T);
             int64_t kb_all = 0;
@@ -281,9 +315,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
                     const int s = (int)(kb_all % STAGES);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
+                    // own A tile, plus both B halves: this CTA's and the peer's
                     mbar_expect_tx(full + s, A_BYTES + B_BYTES);
                     tma_2d(sA + s * A_BYTES, &tA, kb * (F8 ? BK8 : BK), ra, full + s);
-                    tma_2d(sB + s * B_BYTES, &tB, kb * (F8 ? BK8 : BK), rb, full + s);
+                    tma_2d_mc(sB + s * B_BYTES + rank * (B_BYTES / 2), &tB, kb * (F8 ? BK8 : BK),
+                              rb + (int)rank * (BN / 2), full + s, (uint16_t)3);
                 }
             }
             // let every copy issued above land before the CTA can leave
@@ -294,9 +330,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     while (!mbar_try(full + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
                         if (gtimer() - t0 > 1000000000ull) break;
                 }
+                // and both CTAs' releases of those stages (the peer's MMA commits
+                // arrive on this CTA's barriers)
+                for (int64_t q = first; q < kb_all; ++q) {
+                    const uint64_t t0 = gtimer();
+                    while (!mbar_try(empty + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
+                        if (gtimer() - t0 > 1000000000ull) break;
+                }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {  // MMA issuer
             // F32 accumulator; A and B bf16 (kind::f16: type 1) or E4M3 (kind::f8f6f4: type 0)
             const uint32_t ab = F8 ? 0u : 1u;
@@ -328,49 +371,89 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                         else
                             mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                     }
-                    mma_commit(empty + s);
+                    mma_commit_mc(empty + s, (uint16_t)3);
                 }
                 mma_commit(acc_full + b);
                 if (!ok) break;
             }
         }
-    } else {  // epilogue warps 0-3: row 32*warp + lane of each tile
-        // per-warp copy of the tile's column norms (the margin's l_j), read as
+    } else {  // epilogue warps: row 32 (warp % 4) + lane, columns 128 (warp / 4) .. + 127 of each unit
+        const int rg = warp & 3, ch = warp >> 2;
+        // per-warp copy of its 128 column norms (the margin's l_j), read as
         // 128-bit broadcasts
-        float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * BN;
-        UnitWalker walk(a.T);
-        // the column norms l_j of a unit: lane holds columns 8 lane .. 8 lane + 7,
-        // loaded one unit ahead so that their latency hides behind the compare
-        auto load_norms = [&](int jt, float4 &n0, float4 &n1) {
-            const int j = jt + 8 * lane;
-            if (a.l1 && j + 7 < a.n) {
-                n0 = *(const float4 *)(a.l1 + j);
-                n1 = *(const float4 *)(a.l1 + j + 4);
-            } else {
-                float q[8];
+        float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * (BN / 2);
+        int2 *sbuf = (int2 *)(smem + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * (BN / 2) * sizeof(float)) +
+                     warp * SBUF;
+        int nbuf = 0;  // warp-uniform fill of sbuf
+        // write the staged survivors: each lane checks up to SBUF / 32 entries against
+        // the stored couplings (independent loads), then one reservation for the warp
+        auto flush = [&]() {
+            uint32_t keep = 0;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) q[u] = (a.l1 && j + u < a.n) ? a.l1[j + u] : 0.f;
+            for (int u = 0; u < SBUF / 32; ++u) {
+                const int e = 32 * u + lane;
+                if (e < nbuf) {
+                    const int2 pr = sbuf[e];
+                    if (!(a.skip_stored && wt_contains(a.W, pair_key(pr.x, pr.y)))) keep |= 1u << u;
+                }
+            }
+            int kc = __popc(keep), incl = kc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 0 && total) base = atomicAdd(a.count, (unsigned long long)total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int64_t pos = (int64_t)base + incl - kc;
+#pragma unroll
+            for (int u = 0; u < SBUF / 32; ++u) {
+                if (keep >> u & 1u) {
+                    if (pos < a.cap) {
+                        const int2 pr = sbuf[32 * u + lane];
+                        a.out[2 * pos] = pr.x;
+                        a.out[2 * pos + 1] = pr.y;
+                    }
+                    ++pos;
+                }
+            }
+            __syncwarp();
+            nbuf = 0;
+        };
+        UnitWalker walk(a.T);
+        // the column norms l_j of a unit: lane holds columns 4 lane .. 4 lane + 3 of
+        // the warp's half, loaded one unit ahead so that their latency hides
+        // behind the compare
+        auto load_norms = [&](int jt, float4 &n0) {
+            const int j = jt + (BN / 2) * ch + 4 * lane;
+            if (a.l1 && j + 3 < a.n) {
+                n0 = *(const float4 *)(a.l1 + j);
+            } else {
+                float q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) q[u] = (a.l1 && j + u < a.n) ? a.l1[j + u] : 0.f;
                 n0 = make_float4(q[0], q[1], q[2], q[3]);
-                n1 = make_float4(q[4], q[5], q[6], q[7]);
             }
         };
         auto load_row = [&](int ra_) {
-            const int i_ = ra_ + 32 * warp + lane;
+            const int i_ = ra_ + 32 * rg + lane;
             return (a.l1 && i_ < a.n) ? a.l1[i_] : 0.f;
         };
         int ra = 0, jt = 0;
-        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f);
         float li_n = 0.f;
         if ((int64_t)blockIdx.x < a.ntiles) {
             walk.map(blockIdx.x, ra, jt);
-            load_norms(jt, n0, n1);
+            load_norms(jt, n0);
             li_n = load_row(ra);
         }
         int64_t it = 0;
         for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
             const int b = (int)(it & 1);
-            const int i = ra + 32 * warp + lane;
-            const int jt_cur = jt;
+            const int i = ra + 32 * rg + lane;
+            const int jt_cur = jt + (BN / 2) * ch;
             // keep iff |g| > lambda - margin, written |g| + s c_j > thr:
             //   sum margin     rel (l_i + l_j):  c_j = rel l_j, s = 1,        thr = lambda - rel l_i
             //   product margin rel l_i l_j:      c_j = l_j,     s = rel l_i,  thr = lambda
@@ -379,50 +462,59 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             const float thr = (a.product_margin ? a.lambda : a.lambda - a.rel_err * li) - a.abs_margin;
             const float f = a.product_margin ? 1.f : a.rel_err;
             const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
-            const float4 c1 = make_float4(f * n1.x, f * n1.y, f * n1.z, f * n1.w);
-            ((float4 *)cn)[2 * lane] = c0;
-            ((float4 *)cn)[2 * lane + 1] = c1;
-            float cmax = fmaxf(fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w)), fmaxf(fmaxf(c1.x, c1.y), fmaxf(c1.z, c1.w)));
+            ((float4 *)cn)[lane] = c0;
+            float cmax = fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
             // the next unit's mapping and norms, in flight during this unit's compare
             if (t + gridDim.x < a.ntiles) {
                 walk.map(t + gridDim.x, ra, jt);
-                load_norms(jt, n0, n1);
+                load_norms(jt, n0);
                 li_n = load_row(ra);
             }
             __syncwarp();
-            if (!mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort)) break;
+            // all lanes leave together: the loads and shuffles below are warp-wide
+            if (!__all_sync(0xffffffffu, mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort))) break;
             tc_fence_after();
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * BN);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * rg) << 16) + (uint32_t)(b * BN + (BN / 2) * ch);
             // 64 columns at a time from registers: max |g| against the unit's loosest
             // threshold (thr - s max c_j); only a thread whose row passes that test
-            // checks its 64 columns exactly, counts its survivors, reserves their
-            // slots with one atomic and writes them
+            // checks its 64 columns exactly; the warp then stages its survivors
 #pragma unroll 1
-            for (int hf = 0; hf < BN / 64; ++hf) {
+            for (int hf = 0; hf < BN / 128; ++hf) {
                 uint32_t r[64];
                 const uint32_t ta = taddr + (uint32_t)(64 * hf);
                 TMEM_LD32(r, ta);
                 TMEM_LD32((r + 32), ta + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float m = 0.f;
+                // eight independent running maxima (a single chain would serialise
+                // 64 dependent max operations)
+                float m8[8];
 #pragma unroll
-                for (int q = 0; q < 64; ++q) m = fmaxf(m, fabsf(__uint_as_float(r[q])));
+                for (int u = 0; u < 8; ++u) m8[u] = fabsf(__uint_as_float(r[u]));
+#pragma unroll
+                for (int q = 8; q < 64; ++q) m8[q & 7] = fmaxf(m8[q & 7], fabsf(__uint_as_float(r[q])));
+                const float m = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
+                                      fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+                unsigned long long mk = 0;
+                const int j0 = jt_cur + 64 * hf;
                 if (m + sc * cmax > thr) {
                     // exact test of the 64 columns as a bit mask (branch-free), then
                     // j > i, j < n and the stored couplings, then one reservation
                     const float4 *c4p = (const float4 *)(cn + 64 * hf);
-                    const int j0 = jt_cur + 64 * hf;
-                    unsigned long long mk = 0;
+                    // two 32-bit halves, four partial masks each: short dependency chains
+                    uint32_t mw[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
 #pragma unroll
                     for (int q4 = 0; q4 < 16; ++q4) {
                         const float4 c4 = c4p[q4];
-                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr) << (4 * q4 + 0);
-                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr) << (4 * q4 + 1);
-                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr) << (4 * q4 + 2);
-                        mk |= (unsigned long long)(fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr) << (4 * q4 + 3);
+                        const int h = q4 >> 3, sh = 4 * (q4 & 7);
+                        mw[h][0] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr) << (sh + 0);
+                        mw[h][1] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr) << (sh + 1);
+                        mw[h][2] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr) << (sh + 2);
+                        mw[h][3] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr) << (sh + 3);
                     }
+                    mk = (unsigned long long)((mw[0][0] | mw[0][1]) | (mw[0][2] | mw[0][3])) |
+                         ((unsigned long long)((mw[1][0] | mw[1][1]) | (mw[1][2] | mw[1][3])) << 32);
                     const int below = i - j0;  // columns q <= below have j <= i
                     if (below >= 63)
                         mk = 0;
@@ -433,6 +525,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                         mk = 0;
                     else if (valid < 64)
                         mk &= ~0ull >> (64 - valid);
+                }
+                const int cnt = __popcll(mk);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (total > SBUF) {
+                    // more than a batch at once (a penalty the screen cannot cut):
+                    // each thread filters and reserves for itself
                     if (a.skip_stored) {  // stored couplings come separately
                         for (unsigned long long mm = mk; mm; mm &= mm - 1) {
                             const int q = __ffsll((long long)mm) - 1;
@@ -449,16 +553,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                             }
                         }
                     }
+                } else if (total > 0) {
+                    if (nbuf + total > SBUF) flush();
+                    int e = nbuf + incl - cnt;
+                    for (; mk; mk &= mk - 1, ++e) sbuf[e] = make_int2(i, j0 + (__ffsll((long long)mk) - 1));
+                    __syncwarp();
+                    nbuf += total;
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty + b);
         }
+        if (nbuf) flush();
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 5) {
+    cluster_sync();  // neither CTA leaves while the other may still write to it
+    if (warp == MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
@@ -604,7 +716,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
     const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t strides[1] = {(cuuint64_t)K * (fp8 ? 1 : 2)};
-    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN};
+    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN / 2};
     cuuint32_t es[2] = {1, 1};
     if (g_encode(&ta, dt, 2, const_cast<void *>(A), dims, strides, box_a, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -613,12 +725,33 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + 4 * BN * sizeof(float);
-    static int attr_device[2] = {-1, -1};  // per device and variant; set once for each
+    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * (BN / 2) * sizeof(float) +
+                        EPI_WARPS * SBUF * sizeof(int2);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // per device and variant, once: the shared-memory opt-in and how many CTA
+    // pairs fit at a time
+    static int attr_device[2] = {-1, -1}, max_pairs[2] = {0, 0};
     if (attr_device[fp8] != c->device) {
         cudaError_t e = fp8 ? cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                             : cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3(2 * (unsigned)std::max(1, c->num_sms / 2));
+        int np = 0;
+        e = fp8 ? cudaOccupancyMaxActiveClusters(&np, k_screen<true>, &cfg)
+                : cudaOccupancyMaxActiveClusters(&np, k_screen<false>, &cfg);
+        if (e != cudaSuccess) return e;
+        if (np < 1) return cudaErrorLaunchOutOfResources;
+        max_pairs[fp8] = np;
         attr_device[fp8] = c->device;
     }
     ScreenArgs a;
@@ -639,12 +772,14 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.count = count;
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
-    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);
-    if (fp8)
-        k_screen<true><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
-    else
-        k_screen<false><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    // one CTA pair per super-tile at a time, persistent: CTA 2 p + h takes half h
+    // of super-tiles p, p + pairs, ... (units 2 st + h)
+    const int64_t pairs = std::min<int64_t>(a.ntiles / 2, (int64_t)max_pairs[fp8]);
+    cfg.gridDim = dim3((unsigned)(2 * std::max<int64_t>(pairs, 1)));
+    cudaError_t e = fp8 ? cudaLaunchKernelEx(&cfg, k_screen<true>, ta, tb, a)
+                        : cudaLaunchKernelEx(&cfg, k_screen<false>, ta, tb, a);
     note_launch();
+    if (e != cudaSuccess) return e;
     if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.ntiles;
     return cudaGetLastError();
 }
