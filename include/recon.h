@@ -104,9 +104,10 @@ typedef struct {
                              (0 selects the default 0.5) */
     int32_t distance;     /* recon_distance: the d(i, j) that the search ranks pairs by */
     int32_t screen_fp8;   /* nonzero (Ising only): the tensor-core screen reads E4M3 operands,
-                             twice the bf16 rate; its margin widens to cover the coarser
-                             rounding (2^-4 relative plus 2^-10 per sample and node), so the
-                             result is still exact, with more survivors to score.
+                             twice the bf16 rate; its margin (each node's actual rounding
+                             error of its residuals, plus an accumulation allowance) widens
+                             with the coarser rounding, so the result is still exact, with
+                             more survivors to score.
                              RECON_GAUSSIAN: recon_init returns RECON_EUNSUPPORTED */
     int32_t reserved[3];  /* zero */
 } recon_options;

@@ -369,7 +369,7 @@ cudaError_t radix_sort_u64(unsigned long long *keys, uint32_t *vals, unsigned lo
 int screen_k(recon_ctx *c, bool fp8);
 cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1, bool fp8);
 float screen_rel_err(int model, int Mp, bool fp8);
-float screen_abs_err_fp8(int64_t M);
+float screen_acc_err(recon_ctx *c, bool fp8);
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
                           unsigned long long *count, float margin_scale, double *flop_out, bool fp8);
 // general form: operands of K columns (a multiple of 64 bf16 or 128 fp8), of which the first

@@ -94,24 +94,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile in
         }
     }
 }
-// the same box into the same shared-memory offset of every CTA in `mask`, each
-// copy signalling the mbarrier at the same offset in its CTA
-__device__ __forceinline__ void tma_2d_mc(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar,
-                                          uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
-        "l"(tm), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -137,14 +119,6 @@ __device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint
 }
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                 : "memory");
-}
-// one arrival, once the MMAs issued so far are done, on the mbarrier at this
-// offset in every CTA of `mask`
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     su32(bar)),
-                 "h"(mask)
                  : "memory");
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -253,7 +227,7 @@ struct ScreenArgs {
     int last_mma;       // MMAs issued for the last k-block (trailing zero padding skipped)
     float lambda;
     float rel_err;      // margin per unit of the per-node norms
-    float abs_margin;   // plus this much (fp8: the subnormal rounding of the residuals)
+    float abs_margin;   // plus this much
     int product_margin; // margin rel_err * l_i * l_j (Gaussian) instead of rel_err * (l_i + l_j)
     const float *l1;    // per-node norms of the margin
     WTable W;           // pairs with a stored coupling are left to the caller
@@ -278,14 +252,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     int *abort = (int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // CTA pairs (clusters of 2) take the two halves of one super-tile: they share
-    // its B rows, each loading one 128-row half and multicasting it to both
-    const uint32_t rank = cluster_rank();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(empty + s, 2);  // a stage is free once both CTAs' MMAs have read it
+            mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full + b, 1);
@@ -302,7 +273,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    cluster_sync();  // the peer's barriers are initialised before any multicast reaches them
     const uint32_t tmem = *tmem_slot;
 
     if (warp == PRODUCER_WARP) {
@@ -315,11 +285,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
                     const int s = (int)(kb_all % STAGES);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
-                    // own A tile, plus both B halves: this CTA's and the peer's
                     mbar_expect_tx(full + s, A_BYTES + B_BYTES);
                     tma_2d(sA + s * A_BYTES, &tA, kb * (F8 ? BK8 : BK), ra, full + s);
-                    tma_2d_mc(sB + s * B_BYTES + rank * (B_BYTES / 2), &tB, kb * (F8 ? BK8 : BK),
-                              rb + (int)rank * (BN / 2), full + s, (uint16_t)3);
+                    tma_2d(sB + s * B_BYTES, &tB, kb * (F8 ? BK8 : BK), rb, full + s);
                 }
             }
             // let every copy issued above land before the CTA can leave
@@ -328,13 +296,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 for (int64_t q = first; q < kb_all; ++q) {
                     const uint64_t t0 = gtimer();
                     while (!mbar_try(full + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
-                        if (gtimer() - t0 > 1000000000ull) break;
-                }
-                // and both CTAs' releases of those stages (the peer's MMA commits
-                // arrive on this CTA's barriers)
-                for (int64_t q = first; q < kb_all; ++q) {
-                    const uint64_t t0 = gtimer();
-                    while (!mbar_try(empty + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
                         if (gtimer() - t0 > 1000000000ull) break;
                 }
             }
@@ -371,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                         else
                             mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                     }
-                    mma_commit_mc(empty + s, (uint16_t)3);
+                    mma_commit(empty + s);
                 }
                 mma_commit(acc_full + b);
                 if (!ok) break;
@@ -463,9 +424,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             const float f = a.product_margin ? 1.f : a.rel_err;
             const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
             ((float4 *)cn)[lane] = c0;
-            float cmax = fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            // the warp's largest c_j in one reduction: c_j >= +0, whose bit patterns
+            // order like the values
+            const float cmax = __uint_as_float(
+                __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w)))));
             // the next unit's mapping and norms, in flight during this unit's compare
             if (t + gridDim.x < a.ntiles) {
                 walk.map(t + gridDim.x, ra, jt);
@@ -526,6 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     else if (valid < 64)
                         mk &= ~0ull >> (64 - valid);
                 }
+                if (!__any_sync(0xffffffffu, mk != 0)) continue;  // the common case: no survivor in the warp
                 const int cnt = __popcll(mk);
                 int incl = cnt;
 #pragma unroll
@@ -569,7 +532,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // neither CTA leaves while the other may still write to it
     if (warp == MMA_WARP) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -577,14 +539,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     if (threadIdx.x == 0 && *abort) atomicOr(a.err + CNT_ERR, (unsigned long long)ERR_TIMEOUT);
 }
 
-// Ising operands: A_i = [r_i | x_i], B_i = [x_i | r_i] (bf16), r = x - t, and
-// l1_i = sum_m |r_i|; padding samples have r = 0
-__global__ void k_prep_ising(IsingView v, __nv_bfloat16 *A, __nv_bfloat16 *B, float *l1) {
+// Ising operands: A_i = [r_i | x_i], B_i = [x_i | r_i] (bf16), r = x - t;
+// padding samples have r = 0.  The spins are exact, so the product's error
+// is |G~_ij - G_ij| <= sum_m |r~_im - r_im| + sum_m |r~_jm - r_jm| plus the
+// accumulation's; each node's share q_i = (e_i + acc sum_m |r_im|)(1 + 2^-10)
+// is written to q (e_i the node's actual rounding error, summed in FP32; the
+// last factor covers that sum's own rounding), and the margin is q_i + q_j.
+__global__ void k_prep_ising(IsingView v, __nv_bfloat16 *A, __nv_bfloat16 *B, float acc, float *q) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= v.N) return;
     const int K = 2 * v.Mp;
-    float s = 0.f;
+    float s = 0.f, e = 0.f;
     for (int m = lane; m < v.Mp; m += 32) {
         const float x = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? -1.f : 1.f;
         const float r = m < v.M ? x - v.t[i * v.Mp + m] : 0.f;
@@ -594,9 +560,11 @@ __global__ void k_prep_ising(IsingView v, __nv_bfloat16 *A, __nv_bfloat16 *B, fl
         B[i * K + m] = xb;
         B[i * K + v.Mp + m] = rb;
         s += fabsf(r);
+        e += fabsf(__bfloat162float(rb) - r);  // exact: both are floats within a factor 2
     }
     s = warp_sum(s);
-    if (lane == 0) l1[i] = s;
+    e = warp_sum(e);
+    if (lane == 0) q[i] = (e + acc * s) * (1.f + 1.f / 1024.f);
 }
 
 // Gaussian operands: A_i = [e_i | x_i], B_i = [x_i | e_i] (bf16), and the
@@ -624,12 +592,13 @@ __global__ void k_prep_gauss(GaussView v, __nv_bfloat16 *A, __nv_bfloat16 *B, fl
 
 // Ising operands in FP8 E4M3 (uint8 codes): the same rows, each padded with
 // zeros to K8 = a multiple of 128 entries; spins are exact, residuals rounded
-// to nearest (saturating, |r| < 2 anyway)
-__global__ void k_prep_ising_fp8(IsingView v, int K8, uint8_t *A, uint8_t *B, float *l1) {
+// to nearest (saturating, |r| < 2 anyway); q as for bf16, with the E4M3
+// rounding errors
+__global__ void k_prep_ising_fp8(IsingView v, int K8, uint8_t *A, uint8_t *B, float acc, float *q) {
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= v.N) return;
-    float s = 0.f;
+    float s = 0.f, e = 0.f;
     for (int m = 2 * v.Mp + lane; m < K8; m += 32) {
         A[i * K8 + m] = 0;
         B[i * K8 + m] = 0;
@@ -637,16 +606,19 @@ __global__ void k_prep_ising_fp8(IsingView v, int K8, uint8_t *A, uint8_t *B, fl
     for (int m = lane; m < v.Mp; m += 32) {
         const float x = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? -1.f : 1.f;
         const float r = m < v.M ? x - v.t[i * v.Mp + m] : 0.f;
-        const uint8_t rb = (uint8_t)__nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8_storage_t rb = __nv_cvt_float_to_fp8(r, __NV_SATFINITE, __NV_E4M3);
         const uint8_t xb = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
-        A[i * K8 + m] = rb;
+        A[i * K8 + m] = (uint8_t)rb;
         A[i * K8 + v.Mp + m] = xb;
         B[i * K8 + m] = xb;
-        B[i * K8 + v.Mp + m] = rb;
+        B[i * K8 + v.Mp + m] = (uint8_t)rb;
         s += fabsf(r);
+        // the code's value (E4M3 -> half is exact), minus r: exact in FP32
+        e += fabsf(__half2float(__half(__nv_cvt_fp8_to_halfraw(rb, __NV_E4M3))) - r);
     }
     s = warp_sum(s);
-    if (lane == 0) l1[i] = s;
+    e = warp_sum(e);
+    if (lane == 0) q[i] = (e + acc * s) * (1.f + 1.f / 1024.f);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -665,39 +637,44 @@ cudaError_t launch_screen_prep(recon_ctx *c, void *A, void *B, float *l1, bool f
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     if (fp8) {
         if (c->model != RECON_ISING) return cudaErrorInvalidValue;
-        k_prep_ising_fp8<<<grid, 256, 0, c->stream>>>(c->iv(), screen_k(c, true), (uint8_t *)A, (uint8_t *)B, l1);
+        k_prep_ising_fp8<<<grid, 256, 0, c->stream>>>(c->iv(), screen_k(c, true), (uint8_t *)A, (uint8_t *)B,
+                                                       screen_acc_err(c, true), l1);
         note_launch();
         return cudaGetLastError();
     }
     if (c->model == RECON_ISING)
-        k_prep_ising<<<grid, 256, 0, c->stream>>>(c->iv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, l1);
+        k_prep_ising<<<grid, 256, 0, c->stream>>>(c->iv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B,
+                                                  screen_acc_err(c, false), l1);
     else
         k_prep_gauss<<<grid, 256, 0, c->stream>>>(c->gv(), (__nv_bfloat16 *)A, (__nv_bfloat16 *)B, l1);
     note_launch();
     return cudaGetLastError();
 }
 
-// Margin per unit of the operands' norms: bf16 rounding (unit roundoff 2^-8)
-// of one operand (Ising: spins are exact) or both (Gaussian), plus a generous
-// allowance for the f32 accumulation inside the tensor core.
-// Ising: |dg_ij| <= u (|r_i|_1 + |r_j|_1) with u = 2^-8 (the spins are exact),
-//   plus the accumulation error, at most K 2^-23 times the same sum.
-// Gaussian: both operands are rounded, |dg_ij| <= (2u + u^2) sum_m (|e_i x_j| + |x_i e_j|)
+// The screen keeps (i, j) when |G~_ij| + margin_ij > lambda, with margin_ij
+// at least the error of the tensor-core product G~ against the exact G.
+// Ising: the prep kernel writes each node's share q_i of the margin (its
+//   residuals' actual rounding error plus the accumulation allowance), and the
+//   margin is 1 * (q_i + q_j).
+// Gaussian: both operands are rounded to bf16 (unit roundoff u = 2^-8),
+//   |dg_ij| <= (2u + u^2) sum_m (|e_i x_j| + |x_i e_j|)
 //   <= (2u + u^2)(|e_i|_2 |x_j|_2 + |x_i|_2 |e_j|_2) <= (2u + u^2) l_i l_j with
 //   l = |e|_2 + |x|_2 (Cauchy-Schwarz), plus the accumulation error.
 float screen_rel_err(int model, int Mp, bool fp8) {
+    (void)fp8;
+    if (model == RECON_ISING) return 1.f;
     const double u = 1.0 / 256.0, acc = 2.0 * Mp * 1.2e-7;
-    // E4M3: 3 stored mantissa bits, |dr| <= 2^-4 |r| + ...; the products are
-    // exact, and the accumulation is charged 2^-12 of the running magnitude per
-    // MMA (K = 32), which also covers an accumulator narrower than FP32
-    if (fp8) return (float)(1.0 / 16.0 + (2.0 * Mp / 32.0 + 1.0) / 4096.0);
-    if (model == RECON_ISING) return (float)(u + acc);
     return (float)(2 * u + u * u + acc);
 }
 
-// ... + 2^-10 per residual below the smallest normal (2^-6, subnormal spacing
-// 2^-9): sum_m (|dr_i| + |dr_j|) gains at most 2 M 2^-10
-float screen_abs_err_fp8(int64_t M) { return (float)(2.0 * (double)M / 1024.0); }
+// The accumulation allowance per unit of sum_m |r_im| (the products r~ x are
+// exact): bf16, K = 2 Mp FP32 additions, each off by at most 2^-24 of the
+// running magnitude (charged 2^-23); E4M3, 2^-12 of the running magnitude per
+// MMA (K = 32), which also covers an accumulator narrower than FP32.
+float screen_acc_err(recon_ctx *c, bool fp8) {
+    const double Mp = (double)c->Mp;
+    return fp8 ? (float)((2.0 * Mp / 32.0 + 1.0) / 4096.0) : (float)(2.0 * Mp * 1.2e-7);
+}
 
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
@@ -716,7 +693,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
     const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t strides[1] = {(cuuint64_t)K * (fp8 ? 1 : 2)};
-    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN / 2};
+    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN};
     cuuint32_t es[2] = {1, 1};
     if (g_encode(&ta, dt, 2, const_cast<void *>(A), dims, strides, box_a, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -727,31 +704,11 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
         return cudaErrorInvalidValue;
     const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * (BN / 2) * sizeof(float) +
                         EPI_WARPS * SBUF * sizeof(int2);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = c->stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // per device and variant, once: the shared-memory opt-in and how many CTA
-    // pairs fit at a time
-    static int attr_device[2] = {-1, -1}, max_pairs[2] = {0, 0};
+    static int attr_device[2] = {-1, -1};  // per device and variant; set once for each
     if (attr_device[fp8] != c->device) {
         cudaError_t e = fp8 ? cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                             : cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        cfg.gridDim = dim3(2 * (unsigned)std::max(1, c->num_sms / 2));
-        int np = 0;
-        e = fp8 ? cudaOccupancyMaxActiveClusters(&np, k_screen<true>, &cfg)
-                : cudaOccupancyMaxActiveClusters(&np, k_screen<false>, &cfg);
-        if (e != cudaSuccess) return e;
-        if (np < 1) return cudaErrorLaunchOutOfResources;
-        max_pairs[fp8] = np;
         attr_device[fp8] = c->device;
     }
     ScreenArgs a;
@@ -772,14 +729,12 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.count = count;
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
-    // one CTA pair per super-tile at a time, persistent: CTA 2 p + h takes half h
-    // of super-tiles p, p + pairs, ... (units 2 st + h)
-    const int64_t pairs = std::min<int64_t>(a.ntiles / 2, (int64_t)max_pairs[fp8]);
-    cfg.gridDim = dim3((unsigned)(2 * std::max<int64_t>(pairs, 1)));
-    cudaError_t e = fp8 ? cudaLaunchKernelEx(&cfg, k_screen<true>, ta, tb, a)
-                        : cudaLaunchKernelEx(&cfg, k_screen<false>, ta, tb, a);
+    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);  // persistent: one CTA per SM
+    if (fp8)
+        k_screen<true><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    else
+        k_screen<false><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();
-    if (e != cudaSuccess) return e;
     if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.ntiles;
     return cudaGetLastError();
 }
@@ -787,6 +742,6 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,
                           unsigned long long *count, float margin_scale, double *flop_out, bool fp8) {
     return launch_screen_ex(c, A, B, screen_k(c, fp8), (float)c->opt.lambda, l1, margin_scale,
-                            c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out, fp8,
-                            fp8 ? screen_abs_err_fp8(c->M) : 0.f, 2 * (int)c->Mp);
+                            c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out, fp8, 0.f,
+                            2 * (int)c->Mp);
 }

@@ -86,13 +86,15 @@ def test_screen_best_equals_exhaustive(R, N, M, kappa, fp8):
     assert np.allclose(d1[:n], d2[:n], rtol=1e-5, atol=1e-5 * abs(d2.min()))
 
 
-def test_screen_with_couplings_and_in_gcd(R, oracle):
+@pytest.mark.parametrize("fp8", [0, 1])
+def test_screen_with_couplings_and_in_gcd(R, oracle, fp8):
     """After GCD steps W is nonzero: stored couplings are rescored too, and a
     screen-driven GCD reaches the oracle's optimum."""
     N, M = 60, 300
     X = _wl(N, M, 301)
     lam = inputs.default_lambda(N, M, 0.5)
-    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN,
+                  screen_fp8=fp8)
     for _ in range(400):
         delta, obj, m = scr.gcd_step(4, 1.0)
         if delta < 1e-6:
@@ -145,3 +147,28 @@ def test_fp8_screen_is_refused_for_the_gaussian_model(R):
     with pytest.raises(R.ReconError) as e:
         R.Recon(X, R.RECON_GAUSSIAN, lam=1.0, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=1)
     assert e.value.status == R.RECON_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("fp8", [0, 1])
+def test_screen_after_gcd_steps_equals_exhaustive(R, fp8):
+    """With couplings set (residuals vary per sample, so every rounding error
+    differs), the screen's best pairs still equal the exhaustive search's."""
+    N, M = 700, 400
+    X = _wl(N, M, 77)
+    Xs = np.ascontiguousarray(X.T)
+    lam = inputs.default_lambda(N, M)
+    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
+    for _ in range(3):
+        scr.gcd_step(8, 1.0)
+    ij, w, h = scr.get_model()
+    assert len(ij) > 0
+    ex = R.Recon(Xs, R.RECON_ISING, lam=lam)
+    ex.set_model(ij, w, h)
+    p1, d1 = scr.best_pairs(8, 1.0)
+    p2, d2 = ex.exhaustive_best(N)
+    pos2 = d2 < -1e-6 * max(-d2.min(), 1e-30)
+    cut = d2[pos2].max() if pos2.any() else 0.0
+    strict = {tuple(x) for x, dv in zip(p2.tolist(), d2) if dv < cut - 1e-4 * abs(cut)}
+    assert strict <= {tuple(x) for x in p1.tolist()}
+    n = min(len(d1), len(d2))
+    assert np.allclose(d1[:n], d2[:n], rtol=1e-5, atol=1e-5 * abs(d2.min()))
