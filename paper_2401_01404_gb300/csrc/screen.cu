@@ -323,14 +323,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * B_BYTES);
                     // four MMAs per 128-byte k-block row (K = 16 bf16 or 32 fp8 each, 32 bytes
                     // apart: +2 in the descriptor's 16-byte address units)
-                    const int nm = kb + 1 == a.nk ? a.last_mma : 4;
+                    // (straight-line issue: a data-dependent branch between the MMAs of a
+                    // k-block cost the bf16 path about a tenth of its throughput)
+                    if constexpr (F8) {
+                        if (kb + 1 < a.nk || a.last_mma == 4) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (k >= nm) break;
-                        if constexpr (F8)
-                            mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
-                        else
-                            mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                            for (int k = 0; k < 4; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        } else {
+                            for (int k = 0; k < a.last_mma; ++k)
+                                mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                     }
                     mma_commit(empty + s);
                 }
@@ -683,6 +688,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     const int bke = fp8 ? BK8 : BK;  // elements per 128-byte k-block row
     const int kchunk = fp8 ? 32 : 16;  // elements per MMA
     if (K % bke || k_valid <= K - bke || k_valid > K || k_valid % kchunk) return cudaErrorInvalidValue;
+    if (!fp8 && k_valid != K) return cudaErrorInvalidValue;  // the bf16 path issues whole k-blocks
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&g_encode, 12000,
