@@ -157,7 +157,8 @@ static recon_status table_reserve(recon_ctx *c, int64_t extra) {
 static void free_ctx(recon_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void *ps[] = {c->xbits, c->phi, c->t, c->h, c->H, c->xg, c->e, c->mu, c->s2, c->Q, c->W.keys, c->W.vals, c->cnt};
+    void *ps[] = {c->xbits, c->xbitsT, c->phi, c->t,      c->h,      c->H,     c->xg,
+                  c->e,     c->mu,     c->s2,  c->Q, c->W.keys, c->W.vals, c->cnt};
     for (void *p : ps)
         if (p) cudaFree(p);
     if (c->cnt_host) cudaFreeHost(c->cnt_host);
@@ -217,11 +218,13 @@ static recon_status build_state(recon_ctx *c, const void *X, int x_is_device) {
     const size_t rows = (size_t)N * c->Mp * sizeof(float);
     if (c->model == RECON_ISING) {
         ALLOC(c->xbits, (size_t)N * c->Mw * sizeof(uint32_t));
+        ALLOC(c->xbitsT, (size_t)N * 32 * sizeof(uint32_t));
         ALLOC(c->phi, rows);
         ALLOC(c->t, rows);
         ALLOC(c->h, N * sizeof(float));
         ALLOC(c->H, N * sizeof(float));
         CK(launch_ising_pack((const int8_t *)Xd, M, N, (int)c->Mw, c->xbits, c->cnt, c->stream));
+        CK(launch_ising_transpose_bits(c->iv(), c->xbitsT, c->stream));
         CK(launch_ising_init_fields(c->iv(), c->opt.h_clamp, c->stream));
     } else {
         ALLOC(c->xg, rows);

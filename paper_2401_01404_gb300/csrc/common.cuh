@@ -173,6 +173,9 @@ struct IsingView {
     const uint32_t *xbits;
     float *phi, *t, *h, *H;
     int N, M, Mp, Mw;
+    // the same bits transposed per node (32 words): word l holds, at bit c, the
+    // spin of sample 32 c + l (the sample lane l handles in word c)
+    const uint32_t *xT;
 };
 
 struct GaussView {
@@ -215,6 +218,7 @@ struct recon_ctx {
 
     // Ising
     uint32_t *xbits = nullptr;
+    uint32_t *xbitsT = nullptr;  // N x 32 words, see IsingView::xT
     float *phi = nullptr, *t = nullptr, *h = nullptr, *H = nullptr;
     // Gaussian
     float *xg = nullptr, *e = nullptr, *mu = nullptr, *s2 = nullptr, *Q = nullptr;
@@ -254,7 +258,7 @@ struct recon_ctx {
     std::vector<cudaEvent_t> event_pool;
 
     IsingView iv() const {
-        return IsingView{xbits, phi, t, h, H, (int)N, (int)M, (int)Mp, (int)Mw};
+        return IsingView{xbits, phi, t, h, H, (int)N, (int)M, (int)Mp, (int)Mw, xbitsT};
     }
     GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
     bool force_exact = false;  // exact gains even in gradient-distance mode (proposal targets)
@@ -294,6 +298,7 @@ static inline T *buf(recon_ctx *c, int slot) {
 // launchers (each returns cudaGetLastError())
 // ---------------------------------------------------------------------------
 // ising.cu
+cudaError_t launch_ising_transpose_bits(IsingView v, uint32_t *xT, cudaStream_t s);
 cudaError_t launch_ising_pack(const int8_t *X_sm, int64_t M, int64_t N, int Mw, uint32_t *xbits,
                               unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_ising_init_fields(IsingView v, float h_clamp, cudaStream_t s);

@@ -253,37 +253,59 @@ struct SmemRows {
 // disagreeing spins by popcount of whole words.  Every load of row j is issued
 // before any is used (NW >= Mw words, Mw <= 32): lane c holds word c of x_j's
 // bits and shares it by shuffle, so a candidate costs one round trip to L2.
+// Pass 0 of the segmented scorer with row i in registers and both rows' spins
+// as transposed bit columns (bit c of lane l's word: sample 32 c + l):
+//   su = sum_m x_j t_i = T_i - 2 sum_{x_j = -1} t_i,
+//   sv = sum_m x_i t_j = sum_m t_j - 2 sum_{x_i = -1} t_j,
+//   dis = the samples where x_i != x_j;
+// per sample one load and three adds, two of them predicated on a spin bit.
+// Issued in two halves, so that other loads can be in flight between them.
 template <int NW>
-__device__ __forceinline__ void pass0_staged_all(const float *st, const float *sx, const uint32_t *sb,
-                                                 const float *Tj, const uint32_t *Bj, int Mw, int lane, float &su,
-                                                 float &sv, int &dis) {
-    float t[NW];
-    const uint32_t wl = lane < Mw ? __ldg(Bj + lane) : 0u;
+__device__ __forceinline__ void pass0_issue(const float *Tj, const uint32_t *XTj, int Mw, int lane, float (&t)[NW],
+                                            uint32_t &cj) {
+    cj = __ldg(XTj + lane);
 #pragma unroll
     for (int c = 0; c < NW; ++c) t[c] = c < Mw ? __ldg(Tj + 32 * c + lane) : 0.f;
-    const int d = lane < Mw ? __popc(sb[lane] ^ wl) : 0;
-    float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+}
+template <int NW>
+__device__ __forceinline__ void pass0_consume(const float (&ti)[NW], float Ti, uint32_t ci, const float (&t)[NW],
+                                              uint32_t cj, float &su, float &sv, int &dis) {
+    float tot0 = 0.f, tot1 = 0.f, sj0 = 0.f, sj1 = 0.f, si0 = 0.f, si1 = 0.f;
 #pragma unroll
-    for (int c = 0; c < NW; ++c) {
-        if (c < Mw) {
-            const uint32_t w = __shfl_sync(0xffffffffu, wl, c);
-            if (c & 1) {
-                b1 = fmaf(sx[32 * c + lane], t[c], b1);
-                a1 += flip(st[32 * c + lane], (w << (31 - lane)) & 0x80000000u);
-            } else {
-                b0 = fmaf(sx[32 * c + lane], t[c], b0);
-                a0 += flip(st[32 * c + lane], (w << (31 - lane)) & 0x80000000u);
-            }
+    for (int c = 0; c < NW; c += 2) {
+        tot0 += t[c];
+        if (ci & (1u << c)) sj0 += t[c];
+        if (cj & (1u << c)) si0 += ti[c];
+        if (c + 1 < NW) {
+            tot1 += t[c + 1];
+            if (ci & (2u << c)) sj1 += t[c + 1];
+            if (cj & (2u << c)) si1 += ti[c + 1];
         }
     }
-    su = warp_sum(a0 + a1);
-    sv = warp_sum(b0 + b1);
-    dis = warp_sum_i(d);
+    su = Ti - 2.f * warp_sum(si0 + si1);
+    sv = warp_sum((tot0 + tot1) - 2.f * (sj0 + sj1));
+    dis = warp_sum_i(__popc(ci ^ cj));
 }
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+
+// the per-node bit columns of IsingView::xT: one warp per node, lane l holding
+// word l; lane k keeps the ballot of bit k, whose bit c is bit k of word c
+__global__ void k_transpose_bits(IsingView v, uint32_t *xT) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const uint32_t w = lane < v.Mw ? v.xbits[i * v.Mw + lane] : 0u;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t b = __ballot_sync(0xffffffffu, (w >> k) & 1u);
+        if (lane == k) mine = b;
+    }
+    xT[i * 32 + lane] = mine;
+}
 
 __global__ void k_pack(const int8_t *X, int64_t M, int64_t N, int Mw, uint32_t *xbits,
                        unsigned long long *cnt) {
@@ -405,7 +427,7 @@ __global__ void k_objective(IsingView v, double *partials) {
 // cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
 // in shared memory once; each warp streams the rows of its candidates.
 template <int NW>
-__global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+__global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                                    const int64_t *seg_start, const int32_t *seg_count,
                                                    const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
                                                    const int32_t *gid, float *d_out, unsigned long long *cnt) {
@@ -432,17 +454,49 @@ __global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreP
     const int64_t start = seg_start[sidx];
     const int vbase = seg_vbase ? seg_vbase[sidx] : 0;
     unsigned long long npass = 0;
-    for (int q = warp; q < count; q += nw) {
+    // row i in registers for pass 0: lane l holds samples 32 c + l
+    float ti[NW];
+    float Ti = 0.f;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        ti[c] = c < v.Mw ? st[32 * c + lane] : 0.f;
+        Ti += ti[c];
+    }
+    Ti = warp_sum(Ti);
+    const uint32_t ci = __ldg(v.xT + (int64_t)gx * 32 + lane);
+    // Software pipeline over the warp's candidates: while the row loads of
+    // candidate q are in flight, the next candidate's id chain (list entry,
+    // global id, stored coupling, field) resolves, and the list entry of the
+    // one after that is already loaded.
+    auto entry = [&](int q) { return q < count ? (cand ? __ldg(cand + 2 * (start + q) + 1) : vbase + q) : 0; };
+    int q = warp;
+    int gj = 0;
+    float W0 = 0.f, Hj = 0.f;
+    if (q < count) {
+        const int vl = entry(q);
+        gj = gid ? gid[vl] : vl;
+        W0 = wt_lookup(W, pair_key(gx, gj));
+        Hj = v.H[gj];
+    }
+    int vl_next = entry(q + nw);
+    for (; q < count; q += nw) {
         const int64_t pos = start + q;
-        const int vl = cand ? cand[2 * pos + 1] : vbase + q;
-        const int gj = gid ? gid[vl] : vl;
-        const float W0 = wt_lookup(W, pair_key(gx, gj));
-        const float Hj = v.H[gj];
         const float *Tj = v.t + (int64_t)gj * v.Mp;
         const uint32_t *Bj = v.xbits + (int64_t)gj * v.Mw;
+        float tj[NW];
+        uint32_t cj;
+        pass0_issue<NW>(Tj, v.xT + (int64_t)gj * 32, v.Mw, lane, tj, cj);
+        int gj_n = 0;
+        float W0_n = 0.f, Hj_n = 0.f;
+        if (q + nw < count) {
+            gj_n = gid ? gid[vl_next] : vl_next;
+            vl_next = entry(q + 2 * nw);
+            W0_n = wt_lookup(W, pair_key(gx, gj_n));
+            Hj_n = v.H[gj_n];
+        }
         float su, sv;
         int dis;
-        pass0_staged_all<NW>(st, sx, sb, Tj, Bj, v.Mw, lane, su, sv, dis);
+        pass0_consume<NW>(ti, Ti, ci, tj, cj, su, sv, dis);
         SmemRows R{st, sb, Tj, Bj, v.Mw, lane};
         float g, w;
         int passes = 0;
@@ -454,6 +508,9 @@ __global__ void __launch_bounds__(512) k_score_seg(IsingView v, WTable W, ScoreP
             d_out[pos] = -g;
             npass += (unsigned long long)passes;
         }
+        gj = gj_n;
+        W0 = W0_n;
+        Hj = Hj_n;
     }
     if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
 }
@@ -678,6 +735,11 @@ cudaError_t launch_ising_pack(const int8_t *X_sm, int64_t M, int64_t N, int Mw, 
                               unsigned long long *cnt, cudaStream_t s) {
     int64_t warps = ((N + 31) / 32) * Mw;
     k_pack<<<grid_for(warps), 256, 0, s>>>(X_sm, M, N, Mw, xbits, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_transpose_bits(IsingView v, uint32_t *xT, cudaStream_t s) {
+    k_transpose_bits<<<grid_for(v.N), 256, 0, s>>>(v, xT); note_launch();
     return cudaGetLastError();
 }
 
