@@ -225,6 +225,7 @@ static recon_status build_state(recon_ctx *c, const void *X, int x_is_device) {
         ALLOC(c->H, N * sizeof(float));
         CK(launch_ising_pack((const int8_t *)Xd, M, N, (int)c->Mw, c->xbits, c->cnt, c->stream));
         CK(launch_ising_transpose_bits(c->iv(), c->xbitsT, c->stream));
+        CK(ising_score_seg_setup());
         CK(launch_ising_init_fields(c->iv(), c->opt.h_clamp, c->stream));
     } else {
         ALLOC(c->xg, rows);

@@ -169,6 +169,41 @@ enum { ERR_BAD_SPIN = 1, ERR_TABLE_FULL = 2, ERR_BAD_VALUE = 4, ERR_OVERFLOW = 8
 // ---------------------------------------------------------------------------
 // model views passed to kernels
 // ---------------------------------------------------------------------------
+// shared-memory barriers and bulk copies (the tensor-core screen and the
+// staged pair scorer)
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t par) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    return ok != 0;
+}
+// one contiguous global -> shared copy (16-byte aligned ends), its bytes
+// counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(bar))
+                 : "memory");
+}
+
 struct IsingView {
     const uint32_t *xbits;
     float *phi, *t, *h, *H;
@@ -299,6 +334,7 @@ static inline T *buf(recon_ctx *c, int slot) {
 // ---------------------------------------------------------------------------
 // ising.cu
 cudaError_t launch_ising_transpose_bits(IsingView v, uint32_t *xT, cudaStream_t s);
+cudaError_t ising_score_seg_setup();
 cudaError_t launch_ising_pack(const int8_t *X_sm, int64_t M, int64_t N, int Mw, uint32_t *xbits,
                               unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_ising_init_fields(IsingView v, float h_clamp, cudaStream_t s);

@@ -233,6 +233,23 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
 }
 
 // Row i staged in shared memory (t and the sign bits), row j streamed.
+// both rows in shared memory (row j in a staging buffer), the spins as the
+// lane's transposed bit columns: the Newton passes of a staged candidate touch
+// no global memory
+struct StageRows {
+    static constexpr int kNW = 0;
+    const float *st;  // t_i
+    const float *tj;  // t_j
+    uint32_t ci, cj;  // bit c: the spin of sample 32 c + lane (1: -1)
+    int Mw, lane;
+    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb_) const {
+        a = st[32 * c + lane];
+        b = tj[32 * c + lane];
+        sa = (ci << (31 - c)) & 0x80000000u;
+        sb_ = (cj << (31 - c)) & 0x80000000u;
+    }
+};
+
 struct SmemRows {
     static constexpr int kNW = 0;
     const float *st;     // t_i, shared
@@ -248,25 +265,13 @@ struct SmemRows {
     }
 };
 
-// Pass 0 against a staged row: sv = sum x_i t_j (x_i as +-1 floats in shared
-// memory), su = sum x_j t_i (sign of t_i flipped by x_j's bit), and the count of
-// disagreeing spins by popcount of whole words.  Every load of row j is issued
-// before any is used (NW >= Mw words, Mw <= 32): lane c holds word c of x_j's
-// bits and shares it by shuffle, so a candidate costs one round trip to L2.
 // Pass 0 of the segmented scorer with row i in registers and both rows' spins
 // as transposed bit columns (bit c of lane l's word: sample 32 c + l):
 //   su = sum_m x_j t_i = T_i - 2 sum_{x_j = -1} t_i,
 //   sv = sum_m x_i t_j = sum_m t_j - 2 sum_{x_i = -1} t_j,
 //   dis = the samples where x_i != x_j;
-// per sample one load and three adds, two of them predicated on a spin bit.
-// Issued in two halves, so that other loads can be in flight between them.
-template <int NW>
-__device__ __forceinline__ void pass0_issue(const float *Tj, const uint32_t *XTj, int Mw, int lane, float (&t)[NW],
-                                            uint32_t &cj) {
-    cj = __ldg(XTj + lane);
-#pragma unroll
-    for (int c = 0; c < NW; ++c) t[c] = c < Mw ? __ldg(Tj + 32 * c + lane) : 0.f;
-}
+// per sample one shared-memory load and three adds, two of them predicated
+// on a spin bit.
 template <int NW>
 __device__ __forceinline__ void pass0_consume(const float (&ti)[NW], float Ti, uint32_t ci, const float (&t)[NW],
                                               uint32_t cj, float &su, float &sv, int &dis) {
@@ -425,29 +430,63 @@ __global__ void k_objective(IsingView v, double *partials) {
 // covers node x = seg_node[s] (local id) and candidates at output positions
 // seg_start[s] .. + seg_count[s]; the second node of candidate q is
 // cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
-// in shared memory once; each warp streams the rows of its candidates.
+// in shared memory once (and held in registers for pass 0).  Each warp takes
+// its candidates in chunks of 32: the lanes first resolve the chunk's ids,
+// stored couplings and fields in parallel (one round of dependent loads per
+// chunk, not per pair), then lane 0 keeps SEG_RING candidate rows (t and the
+// bit column) in flight with bulk asynchronous copies into a ring of
+// shared-memory stages, one mbarrier per stage.  Every wait is bounded
+// (about 1 s); a warp that gives up sets ERR_TIMEOUT, lets its copies land
+// (again bounded) and stops.
+constexpr int SEG_RING = 3;
+
+__device__ __forceinline__ bool seg_wait(uint64_t *b, uint32_t par) {
+    if (mbar_try(b, par)) return true;
+    uint64_t t0 = 0;
+    for (uint32_t n = 1;; ++n) {
+        if (mbar_try(b, par)) return true;
+        if ((n & 255u) == 0) {
+            const uint64_t now = gtimer();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > 1000000000ull)
+                return false;
+        }
+    }
+}
+
 template <int NW>
 __global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
-                                                   const int64_t *seg_start, const int32_t *seg_count,
-                                                   const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
-                                                   const int32_t *gid, float *d_out, unsigned long long *cnt) {
-    extern __shared__ float sm[];
+                                                      const int64_t *seg_start, const int32_t *seg_count,
+                                                      const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
+                                                      const int32_t *gid, float *d_out, unsigned long long *cnt) {
+    extern __shared__ __align__(128) float sm[];
     const int64_t sidx = blockIdx.x;
     if (sidx >= nseg) return;
     const int count = seg_count[sidx];
     if (count <= 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // layout: row x (Mp floats), its bits (32 words), per warp SEG_RING stages
+    // of Mp + 32 words, the stages' mbarriers, then per warp the chunk's ids,
+    // stored couplings and fields (32 each)
+    const int stw = v.Mp + 32;
     float *st = sm;
-    float *sx = sm + v.Mp;
-    uint32_t *sb = (uint32_t *)(sm + 2 * v.Mp);
+    uint32_t *sb = (uint32_t *)(sm + v.Mp);
+    float *ring = sm + v.Mp + 32;
+    float *myring = ring + (size_t)warp * SEG_RING * stw;
+    uint64_t *bars0 = (uint64_t *)(ring + (size_t)nw * SEG_RING * stw);
+    uint64_t *bars = bars0 + warp * SEG_RING;
+    int *cgj = (int *)(bars0 + nw * SEG_RING) + warp * 96;
+    float *cW0 = (float *)(cgj + 32), *cHj = (float *)(cgj + 64);
+    if (lane == 0) {
+        for (int r = 0; r < SEG_RING; ++r) mbar_init(bars + r, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     const int x = seg_node[sidx];
     const int gx = gid ? gid[x] : x;
     const float *Tx = v.t + (int64_t)gx * v.Mp;
     const uint32_t *Bx = v.xbits + (int64_t)gx * v.Mw;
-    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) {
-        st[m] = Tx[m];
-        sx[m] = ((Bx[m >> 5] >> (m & 31)) & 1u) ? -1.f : 1.f;
-    }
+    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) st[m] = Tx[m];
     for (int c = threadIdx.x; c < v.Mw; c += blockDim.x) sb[c] = Bx[c];
     __syncthreads();
     const float Hx = v.H[gx];
@@ -464,53 +503,75 @@ __global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, Sco
     }
     Ti = warp_sum(Ti);
     const uint32_t ci = __ldg(v.xT + (int64_t)gx * 32 + lane);
-    // Software pipeline over the warp's candidates: while the row loads of
-    // candidate q are in flight, the next candidate's id chain (list entry,
-    // global id, stored coupling, field) resolves, and the list entry of the
-    // one after that is already loaded.
-    auto entry = [&](int q) { return q < count ? (cand ? __ldg(cand + 2 * (start + q) + 1) : vbase + q) : 0; };
-    int q = warp;
-    int gj = 0;
-    float W0 = 0.f, Hj = 0.f;
-    if (q < count) {
-        const int vl = entry(q);
-        gj = gid ? gid[vl] : vl;
-        W0 = wt_lookup(W, pair_key(gx, gj));
-        Hj = v.H[gj];
+    const uint32_t stage_bytes = (uint32_t)(v.Mp * 4 + 128);
+    const int mine = count > warp ? (count - warp + nw - 1) / nw : 0;  // candidates of this warp
+    // lane 0: the warp's k-th candidate (chunk slot k - base) into stage k % SEG_RING
+    auto issue = [&](int k, int base) {
+        const int s = k % SEG_RING;
+        const int g = cgj[k - base];
+        mbar_expect_tx(bars + s, stage_bytes);
+        bulk_g2s(myring + s * stw, v.t + (int64_t)g * v.Mp, (uint32_t)(v.Mp * 4), bars + s);
+        bulk_g2s(myring + s * stw + v.Mp, v.xT + (int64_t)g * 32, 128u, bars + s);
+    };
+    int k = 0;  // candidates of this warp consumed so far (also its stage sequence number)
+    bool ok = true;
+    for (int base = 0; base < mine && ok; base += 32) {
+        const int nch = min(32, mine - base);
+        {  // the chunk's ids, stored couplings and fields, one candidate per lane
+            const int q = warp + (base + lane) * nw;
+            if (lane < nch) {
+                const int vl = cand ? __ldg(cand + 2 * (start + q) + 1) : vbase + q;
+                const int g = gid ? gid[vl] : vl;
+                cgj[lane] = g;
+                cW0[lane] = wt_lookup(W, pair_key(gx, g));
+                cHj[lane] = v.H[g];
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            for (int r = 0; r < SEG_RING && r < nch; ++r) issue(base + r, base);
+        __syncwarp();
+        for (int u = 0; u < nch; ++u, ++k) {
+            const int q = warp + k * nw;
+            const int64_t pos = start + q;
+            const int s = k % SEG_RING;
+            if (!__all_sync(0xffffffffu, seg_wait(bars + s, (uint32_t)((k / SEG_RING) & 1)))) {
+                ok = false;
+                break;
+            }
+            const int gj = cgj[u];
+            const float W0 = cW0[u], Hj = cHj[u];
+            const float *row = myring + s * stw;
+            float tj[NW];
+#pragma unroll
+            for (int c = 0; c < NW; ++c) tj[c] = c < v.Mw ? row[32 * c + lane] : 0.f;
+            const uint32_t cj = ((const uint32_t *)row)[v.Mp + lane];
+            float su, sv;
+            int dis;
+            pass0_consume<NW>(ti, Ti, ci, tj, cj, su, sv, dis);
+            StageRows R{st, row, ci, cj, v.Mw, lane};
+            float g, w;
+            int passes = 0;
+            if (p.grad_only)
+                g = grad_dist(2.f * (float)(v.Mp - 2 * dis) - su - sv, W0, p.lambda);
+            else
+                solve_from_pass0(R, v.Mp, su, sv, dis, Hx + Hj, W0, p.lambda, p.w_clamp, g, w, passes);
+            if (lane == 0) {
+                d_out[pos] = -g;
+                npass += (unsigned long long)passes;
+            }
+            __syncwarp();  // every lane has read stage s: refill it within the chunk
+            if (lane == 0 && u + SEG_RING < nch) issue(k + SEG_RING, base);
+            __syncwarp();
+        }
     }
-    int vl_next = entry(q + nw);
-    for (; q < count; q += nw) {
-        const int64_t pos = start + q;
-        const float *Tj = v.t + (int64_t)gj * v.Mp;
-        const uint32_t *Bj = v.xbits + (int64_t)gj * v.Mw;
-        float tj[NW];
-        uint32_t cj;
-        pass0_issue<NW>(Tj, v.xT + (int64_t)gj * 32, v.Mw, lane, tj, cj);
-        int gj_n = 0;
-        float W0_n = 0.f, Hj_n = 0.f;
-        if (q + nw < count) {
-            gj_n = gid ? gid[vl_next] : vl_next;
-            vl_next = entry(q + 2 * nw);
-            W0_n = wt_lookup(W, pair_key(gx, gj_n));
-            Hj_n = v.H[gj_n];
-        }
-        float su, sv;
-        int dis;
-        pass0_consume<NW>(ti, Ti, ci, tj, cj, su, sv, dis);
-        SmemRows R{st, sb, Tj, Bj, v.Mw, lane};
-        float g, w;
-        int passes = 0;
-        if (p.grad_only)
-            g = grad_dist(2.f * (float)(v.Mp - 2 * dis) - su - sv, W0, p.lambda);
-        else
-            solve_from_pass0(R, v.Mp, su, sv, dis, Hx + Hj, W0, p.lambda, p.w_clamp, g, w, passes);
-        if (lane == 0) {
-            d_out[pos] = -g;
-            npass += (unsigned long long)passes;
-        }
-        gj = gj_n;
-        W0 = W0_n;
-        Hj = Hj_n;
+    if (!ok && lane == 0) {
+        atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TIMEOUT);
+        // the copies still in flight (issued within the chunk) land before the block can leave
+        const int base = k / 32 * 32;
+        const int nch = min(32, mine - base);
+        for (int kk = k; kk < base + nch && kk < k + SEG_RING; ++kk)
+            seg_wait(bars + kk % SEG_RING, (uint32_t)((kk / SEG_RING) & 1));
     }
     if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
 }
@@ -792,13 +853,34 @@ cudaError_t launch_ising_score(IsingView v, WTable W, ScoreParams p, const int32
     return cudaGetLastError();
 }
 
+namespace {
+constexpr size_t SEG_SMEM_MAX = 227 * 1024;
+size_t seg_smem_bytes(int Mp, int nw) {
+    return sizeof(float) * ((size_t)Mp + 32 + (size_t)nw * SEG_RING * (Mp + 32)) +
+           (size_t)nw * SEG_RING * sizeof(uint64_t) + (size_t)nw * 96 * sizeof(int);
+}
+}  // namespace
+
+// the segmented scorer's shared-memory opt-in, once per device (outside any
+// stream capture)
+cudaError_t ising_score_seg_setup() {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {cudaFuncSetAttribute(k_score_seg<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_MAX),
+                          cudaFuncSetAttribute(k_score_seg<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_MAX),
+                          cudaFuncSetAttribute(k_score_seg<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_MAX),
+                          cudaFuncSetAttribute(k_score_seg<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_MAX)})
+        if (r != cudaSuccess) e = r;
+    return e;
+}
+
 cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                    const int64_t *seg_start, const int32_t *seg_count, const int32_t *seg_vbase,
                                    int64_t nseg, const int32_t *cand, const int32_t *gid, float *d_out,
                                    unsigned long long *cnt, int threads, cudaStream_t s) {
     if (nseg <= 0) return cudaSuccess;
-    size_t smem = sizeof(float) * 2 * v.Mp + sizeof(uint32_t) * v.Mw;
-    if (v.Mw > 32) return cudaErrorInvalidValue;
+    if (v.Mw > 32 || threads < 32 || threads > 512 || threads % 32) return cudaErrorInvalidValue;
+    const size_t smem = seg_smem_bytes(v.Mp, threads / 32);
+    if (smem > SEG_SMEM_MAX) return cudaErrorInvalidValue;
 #define SEG_LAUNCH(NWV)                                                                                              \
     k_score_seg<NWV><<<(unsigned)nseg, threads, smem, s>>>(v, W, p, seg_node, seg_start, seg_count, seg_vbase, nseg, \
                                                            cand, gid, d_out, cnt)

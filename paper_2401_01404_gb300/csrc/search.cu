@@ -733,6 +733,10 @@ static recon_status check_err_flags(recon_ctx *c, const char *where) {
         CKS(cudaMemsetAsync(c->cnt + CNT_ERR, 0, sizeof(unsigned long long), c->stream));
         if (f & ERR_OVERFLOW) return set_err(c, RECON_ENOMEM, "%s: a search buffer overflowed", where);
         if (f & ERR_TABLE_FULL) return set_err(c, RECON_ENOMEM, "%s: a hash table is full", where);
+        if (f & ERR_TIMEOUT) {
+            c->broken = true;
+            return set_err(c, RECON_ETIMEOUT, "%s: a bounded wait on the device ran out", where);
+        }
         return set_err(c, RECON_EINVAL, "%s: device-side check failed (flags %llx)", where, f);
     }
     return RECON_OK;
