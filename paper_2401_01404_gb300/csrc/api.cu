@@ -489,12 +489,19 @@ static recon_status cd_sweep_dev(recon_ctx *c, const int32_t *dp, int64_t P, dou
                              buf<unsigned long long>(c, BUF_SORT1), vals, vals + 2 * P, buf<int64_t>(c, BUF_SORT3),
                              links, links + 2 * P, links + 3 * P, links + 4 * P, buf<int>(c, BUF_BATCH),
                              buf<int>(c, BUF_ORDER), buf<int>(c, BUF_OFF), nb_dev, c->stream));
+    // the batch count and (usually all of) the batch offsets in one round trip
     int nb = 0;
+    const int64_t guess = std::min<int64_t>(P + 1, 257);
+    std::vector<int> off((size_t)guess);
     CK(cudaMemcpyAsync(&nb, nb_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(off.data(), buf<int>(c, BUF_OFF), sizeof(int) * guess, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    std::vector<int> off(nb + 1);
-    CK(cudaMemcpyAsync(off.data(), buf<int>(c, BUF_OFF), sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (nb + 1 > guess) {
+        off.resize(nb + 1);
+        CK(cudaMemcpyAsync(off.data(), buf<int>(c, BUF_OFF), sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     double *delta = buf<double>(c, BUF_DELTA);
     const int *offd = buf<int>(c, BUF_OFF), *order = buf<int>(c, BUF_ORDER);
     // a batch with at most `thin` pairs joins a run of thin batches that one block

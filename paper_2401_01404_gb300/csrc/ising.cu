@@ -26,9 +26,25 @@ constexpr int MAX_NEWTON = 40;
 
 // -------- row sources ------------------------------------------------------
 
+// Sums over a pair's samples: a row source whose words one warp holds reduces
+// with warp shuffles (BlockRows, whose words the warps of a block share,
+// reduces across the block).
+#define WARP_SUMS                                                                    \
+    __device__ __forceinline__ float sum(float a) const { return warp_sum(a); }      \
+    __device__ __forceinline__ void sum2(float &a, float &b) const {                 \
+        a = warp_sum(a);                                                             \
+        b = warp_sum(b);                                                             \
+    }                                                                                \
+    __device__ __forceinline__ void sum3(float &a, float &b, float &c) const {       \
+        a = warp_sum(a);                                                             \
+        b = warp_sum(b);                                                             \
+        c = warp_sum(c);                                                             \
+    }
+
 template <int NW>
 struct RegRows {  // both rows in registers (NW words of 32 samples)
     static constexpr int kNW = NW;
+    WARP_SUMS
     float ti[NW], tj[NW];
     uint32_t pi, pj;  // bit c: x = -1 at sample 32c + lane
     int Mw;
@@ -60,8 +76,86 @@ struct RegRows {  // both rows in registers (NW words of 32 samples)
     }
 };
 
+// Both rows over the warps of a block: warp w holds words w NWW .. w NWW + NWW - 1
+// of each row in registers (lane l: sample 32 c + l); sums reduce across the
+// block through shared memory, in two alternating scratch rows so that one
+// barrier per reduction suffices.  Every warp takes part in every reduction.
+template <int NWW>
+struct BlockRows {
+    static constexpr int kNW = NWW;
+    float ti[NWW], tj[NWW];
+    uint32_t pi, pj;  // bit c: x = -1 at sample 32 (w0 + c) + lane
+    int Mw;           // this warp's words, 0 .. NWW
+    int w0;           // its first word
+    float *red;       // 2 x 3 x nw floats of shared scratch
+    int nw, warp, lane;
+    mutable int phase;
+    __device__ __forceinline__ void setup(float *scratch) {
+        red = scratch;
+        nw = blockDim.x >> 5;
+        warp = threadIdx.x >> 5;
+        lane = threadIdx.x & 31;
+        phase = 0;
+    }
+    template <bool coherent = false>
+    __device__ __forceinline__ void load(const IsingView &v, int i, int j, int) {
+        w0 = warp * NWW;
+        Mw = max(0, min(NWW, v.Mw - w0));
+        const float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
+        const uint32_t *Bi = v.xbits + (int64_t)i * v.Mw, *Bj = v.xbits + (int64_t)j * v.Mw;
+        pi = pj = 0u;
+#pragma unroll
+        for (int c = 0; c < NWW; ++c) {
+            if (c < Mw) {
+                const int g = w0 + c;
+                ti[c] = coherent ? Ti[32 * g + lane] : __ldg(Ti + 32 * g + lane);
+                tj[c] = coherent ? Tj[32 * g + lane] : __ldg(Tj + 32 * g + lane);
+                pi |= ((__ldg(Bi + g) >> lane) & 1u) << c;
+                pj |= ((__ldg(Bj + g) >> lane) & 1u) << c;
+            } else {
+                ti[c] = tj[c] = 1.f;
+            }
+        }
+    }
+    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb) const {
+        a = ti[c];
+        b = tj[c];
+        sa = (pi << (31 - c)) & 0x80000000u;
+        sb = (pj << (31 - c)) & 0x80000000u;
+    }
+    __device__ __forceinline__ void sum3(float &a, float &b, float &c) const {
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        float *r = red + (phase & 1) * 3 * nw;
+        ++phase;
+        if (lane == 0) {
+            r[warp] = a;
+            r[nw + warp] = b;
+            r[2 * nw + warp] = c;
+        }
+        __syncthreads();
+        a = b = c = 0.f;
+        for (int w = 0; w < nw; ++w) {
+            a += r[w];
+            b += r[nw + w];
+            c += r[2 * nw + w];
+        }
+    }
+    __device__ __forceinline__ void sum2(float &a, float &b) const {
+        float z = 0.f;
+        sum3(a, b, z);
+    }
+    __device__ __forceinline__ float sum(float a) const {
+        float y = 0.f, z = 0.f;
+        sum3(a, y, z);
+        return a;
+    }
+};
+
 struct GlobRows {  // rows re-read every pass
     static constexpr int kNW = 0;
+    WARP_SUMS
     const float *Ti, *Tj;
     const uint32_t *Bi, *Bj;
     int Mw, lane;
@@ -120,9 +214,11 @@ __device__ __forceinline__ void pass0(const RS &R, float &su, float &sv, int &di
         b += flip(tj, si);
         d += (int)((si ^ sj) >> 31);
     });
-    su = warp_sum(a);
-    sv = warp_sum(b);
-    dis = warp_sum_i(d);
+    float df = (float)d;  // exact: at most 1024 samples
+    R.sum3(a, b, df);
+    su = a;
+    sv = b;
+    dis = (int)df;
 }
 
 // d1 = sum [(u+tau)/(1+tau u) + (v+tau)/(1+tau v)], d2 = sum [(1-u^2)/(1+tau u)^2 + ...]
@@ -141,8 +237,9 @@ __device__ __forceinline__ void pass_newton(const RS &R, float tau, float &d1, f
         a2 = fmaf(fmaf(-u, u, 1.f), ru * ru, a2);
         a2 = fmaf(fmaf(-v, v, 1.f), rv * rv, a2);
     });
-    d1 = warp_sum(a1);
-    d2 = warp_sum(a2);
+    R.sum2(a1, a2);
+    d1 = a1;
+    d2 = a2;
 }
 
 // q = sum [(delta u - log(1+tau u)) + (delta v - log(1+tau v))]
@@ -157,7 +254,7 @@ __device__ __forceinline__ float pass_gain(const RS &R, float delta, float tau) 
         q += fmaf(delta, u, -log1pf(tau * u));
         q += fmaf(delta, v, -log1pf(tau * v));
     });
-    return warp_sum(q);
+    return R.sum(q);
 }
 
 // The 1-D problem of one pair once its pass at delta = 0 is known (sums of u
@@ -238,6 +335,7 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
 // no global memory
 struct StageRows {
     static constexpr int kNW = 0;
+    WARP_SUMS
     const float *st;  // t_i
     const float *tj;  // t_j
     uint32_t ci, cj;  // bit c: the spin of sample 32 c + lane (1: -1)
@@ -252,6 +350,7 @@ struct StageRows {
 
 struct SmemRows {
     static constexpr int kNW = 0;
+    WARP_SUMS
     const float *st;     // t_i, shared
     const uint32_t *sb;  // x_i sign bits, shared
     const float *Tj;
@@ -539,7 +638,6 @@ __global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, Sco
                 ok = false;
                 break;
             }
-            const int gj = cgj[u];
             const float W0 = cW0[u], Hj = cHj[u];
             const float *row = myring + s * stw;
             float tj[NW];
@@ -618,6 +716,18 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
     const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
     RS R;
     R.template load<true>(v, i, j, lane);
+    // the fields phi of both rows, in flight during the solve (one round trip for
+    // the row update instead of one per chunk of words)
+    constexpr int NWP = RS::kNW > 0 ? RS::kNW : 32;
+    float *Pi = v.phi + (int64_t)i * v.Mp, *Pj = v.phi + (int64_t)j * v.Mp;
+    float pa[NWP], pb[NWP];
+#pragma unroll
+    for (int c = 0; c < NWP; ++c) {
+        const int m = 32 * c + lane;
+        const bool ok = c < v.Mw && m < v.M;
+        pa[c] = ok ? Pi[m] : 0.f;
+        pb[c] = ok ? Pj[m] : 0.f;
+    }
     const uint64_t key = pair_key(i, j);
     const float W0 = wt_lookup(W, key);
     float g, w;
@@ -625,40 +735,24 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
     solve_pair(R, v.Mp, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
     const float dl = w - W0;
     if (dl != 0.f) {
-        const uint32_t *Bi = v.xbits + (int64_t)i * v.Mw, *Bj = v.xbits + (int64_t)j * v.Mw;
-        float *Pi = v.phi + (int64_t)i * v.Mp, *Pj = v.phi + (int64_t)j * v.Mp;
         float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
         float hi = 0.f, hj = 0.f;
-        // words in chunks of UCH: every load of a chunk is in flight before the
-        // first is used (one round trip to L2 per chunk, not per word)
-        constexpr int UCH = 8;
-        for (int c0 = 0; c0 < v.Mw; c0 += UCH) {
-            float pa[UCH], pb[UCH];
-            uint32_t wa[UCH], wb[UCH];
 #pragma unroll
-            for (int q = 0; q < UCH; ++q) {
-                const int c = c0 + q, m = 32 * c + lane;
-                const bool ok = c < v.Mw && m < v.M;
-                pa[q] = ok ? Pi[m] : 0.f;
-                pb[q] = ok ? Pj[m] : 0.f;
-                wa[q] = c < v.Mw ? __ldg(Bi + c) : 0u;
-                wb[q] = c < v.Mw ? __ldg(Bj + c) : 0u;
-            }
-#pragma unroll
-            for (int q = 0; q < UCH; ++q) {
-                const int c = c0 + q, m = 32 * c + lane;
-                if (c < v.Mw && m < v.M) {
-                    const bool xi_neg = (wa[q] >> lane) & 1u, xj_neg = (wb[q] >> lane) & 1u;
-                    const float pi = pa[q] + (xj_neg ? -dl : dl);
-                    const float pj = pb[q] + (xi_neg ? -dl : dl);
-                    const float a = tanhf(pi), b = tanhf(pj);
-                    Pi[m] = pi;
-                    Pj[m] = pj;
-                    Ti[m] = a;
-                    Tj[m] = b;
-                    hi += 1.f - a * a;
-                    hj += 1.f - b * b;
-                }
+        for (int c = 0; c < NWP; ++c) {
+            const int m = 32 * c + lane;
+            if (c < v.Mw && m < v.M) {
+                float a_, b_;
+                uint32_t si, sj;
+                R.get(c, a_, b_, si, sj);  // si, sj: the sign bits of x_i, x_j at m
+                const float pi = pa[c] + (sj ? -dl : dl);
+                const float pj = pb[c] + (si ? -dl : dl);
+                const float a = tanhf(pi), b = tanhf(pj);
+                Pi[m] = pi;
+                Pj[m] = pj;
+                Ti[m] = a;
+                Tj[m] = b;
+                hi += 1.f - a * a;
+                hj += 1.f - b * b;
             }
         }
         hi = warp_sum(hi);
@@ -675,16 +769,68 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
     }
 }
 
-// One matching batch of the update loop: pairs order[begin..end) share no node,
-// so their row updates are independent.
-template <class RS>
-__global__ void __launch_bounds__(256) k_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
-                                                const int32_t *order, int64_t begin, int64_t end,
-                                                double *delta, unsigned long long *cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = begin + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (q >= end) return;
-    update_one<RS>(v, W, p, pairs, order[q], delta, cnt, lane);
+// One matching batch of the update loop (pairs order[begin..end) share no node,
+// so their row updates are independent), one block per pair: the block's warps
+// share the pair's samples (BlockRows), so each Newton pass and the row update
+// take an eighth of a single warp's time.
+template <int NWW>
+__global__ void __launch_bounds__(256) k_update_blk(IsingView v, WTable W, ScoreParams p, const int32_t *pairs,
+                                                    const int32_t *order, int64_t begin, double *delta,
+                                                    unsigned long long *cnt) {
+    __shared__ float red[2 * 3 * 8];
+    const int pidx = order[begin + blockIdx.x];
+    const int i = pairs[2 * pidx], j = pairs[2 * pidx + 1];
+    BlockRows<NWW> R;
+    R.setup(red);
+    R.template load<true>(v, i, j, 0);
+    const int lane = R.lane;
+    float *Pi = v.phi + (int64_t)i * v.Mp, *Pj = v.phi + (int64_t)j * v.Mp;
+    float pa[NWW], pb[NWW];
+#pragma unroll
+    for (int c = 0; c < NWW; ++c) {
+        const int m = 32 * (R.w0 + c) + lane;
+        const bool ok = c < R.Mw && m < v.M;
+        pa[c] = ok ? Pi[m] : 0.f;
+        pb[c] = ok ? Pj[m] : 0.f;
+    }
+    const uint64_t key = pair_key(i, j);
+    const float W0 = wt_lookup(W, key);
+    float g, w;
+    int passes;
+    solve_pair(R, v.Mp, v.H[i] + v.H[j], W0, p.lambda, p.w_clamp, g, w, passes);
+    const float dl = w - W0;
+    if (dl != 0.f) {
+        float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
+        float hi = 0.f, hj = 0.f;
+#pragma unroll
+        for (int c = 0; c < NWW; ++c) {
+            const int m = 32 * (R.w0 + c) + lane;
+            if (c < R.Mw && m < v.M) {
+                float a_, b_;
+                uint32_t si, sj;
+                R.get(c, a_, b_, si, sj);
+                const float pi = pa[c] + (sj ? -dl : dl);
+                const float pj = pb[c] + (si ? -dl : dl);
+                const float a = tanhf(pi), b = tanhf(pj);
+                Pi[m] = pi;
+                Pj[m] = pj;
+                Ti[m] = a;
+                Tj[m] = b;
+                hi += 1.f - a * a;
+                hj += 1.f - b * b;
+            }
+        }
+        R.sum2(hi, hj);
+        if (threadIdx.x == 0) {
+            v.H[i] = hi;
+            v.H[j] = hj;
+            if (!wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
+        }
+    }
+    if (threadIdx.x == 0) {
+        delta[pidx] = fabs((double)dl);
+        atomicAdd(&cnt[CNT_NEWTON], (unsigned long long)passes);
+    }
 }
 
 // Consecutive thin batches b0 .. b1-1 in one block: the batches run in turn,
@@ -901,8 +1047,16 @@ cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int3
                                 int64_t begin, int64_t end, double *delta, unsigned long long *cnt,
                                 cudaStream_t s) {
     if (end <= begin) return cudaSuccess;
-    unsigned grid = grid_for(end - begin);
-    DISPATCH_ROWS(v.Mw, (k_update<RS><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, end, delta, cnt))); note_launch();
+    if (v.Mw > 32) return cudaErrorInvalidValue;
+    // one block of 8 warps per pair, each warp ceil(Mw / 8) words
+    const unsigned grid = (unsigned)(end - begin);
+    if (v.Mw <= 8)
+        k_update_blk<1><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, delta, cnt);
+    else if (v.Mw <= 16)
+        k_update_blk<2><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, delta, cnt);
+    else
+        k_update_blk<4><<<grid, 256, 0, s>>>(v, W, p, pairs, order, begin, delta, cnt);
+    note_launch();
     return cudaGetLastError();
 }
 
