@@ -364,26 +364,26 @@ struct SmemRows {
     }
 };
 
-// Pass 0 of the segmented scorer with row i in registers and both rows' spins
-// as transposed bit columns (bit c of lane l's word: sample 32 c + l):
+// Pass 0 of the segmented scorer with row i staged in shared memory and both
+// rows' spins as transposed bit columns (bit c of lane l's word: sample 32 c + l):
 //   su = sum_m x_j t_i = T_i - 2 sum_{x_j = -1} t_i,
 //   sv = sum_m x_i t_j = sum_m t_j - 2 sum_{x_i = -1} t_j,
 //   dis = the samples where x_i != x_j;
-// per sample one shared-memory load and three adds, two of them predicated
-// on a spin bit.
+// per sample a shared-memory load or two and three adds, two of them
+// predicated on a spin bit.
 template <int NW>
-__device__ __forceinline__ void pass0_consume(const float (&ti)[NW], float Ti, uint32_t ci, const float (&t)[NW],
+__device__ __forceinline__ void pass0_consume(const float *st, int lane, float Ti, uint32_t ci, const float (&t)[NW],
                                               uint32_t cj, float &su, float &sv, int &dis) {
     float tot0 = 0.f, tot1 = 0.f, sj0 = 0.f, sj1 = 0.f, si0 = 0.f, si1 = 0.f;
 #pragma unroll
     for (int c = 0; c < NW; c += 2) {
         tot0 += t[c];
         if (ci & (1u << c)) sj0 += t[c];
-        if (cj & (1u << c)) si0 += ti[c];
+        if (cj & (1u << c)) si0 += st[32 * c + lane];
         if (c + 1 < NW) {
             tot1 += t[c + 1];
             if (ci & (2u << c)) sj1 += t[c + 1];
-            if (cj & (2u << c)) si1 += ti[c + 1];
+            if (cj & (2u << c)) si1 += st[32 * (c + 1) + lane];
         }
     }
     su = Ti - 2.f * warp_sum(si0 + si1);
@@ -537,7 +537,7 @@ __global__ void k_objective(IsingView v, double *partials) {
 // shared-memory stages, one mbarrier per stage.  Every wait is bounded
 // (about 1 s); a warp that gives up sets ERR_TIMEOUT, lets its copies land
 // (again bounded) and stops.
-constexpr int SEG_RING = 3;
+constexpr int SEG_RING = 2;
 
 __device__ __forceinline__ bool seg_wait(uint64_t *b, uint32_t par) {
     if (mbar_try(b, par)) return true;
@@ -554,8 +554,9 @@ __device__ __forceinline__ bool seg_wait(uint64_t *b, uint32_t par) {
     }
 }
 
+// (at most 80 registers: with 256 threads, three blocks fit on an SM)
 template <int NW>
-__global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
+__global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p, const int32_t *seg_node,
                                                       const int64_t *seg_start, const int32_t *seg_count,
                                                       const int32_t *seg_vbase, int64_t nseg, const int32_t *cand,
                                                       const int32_t *gid, float *d_out, unsigned long long *cnt) {
@@ -592,14 +593,10 @@ __global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, Sco
     const int64_t start = seg_start[sidx];
     const int vbase = seg_vbase ? seg_vbase[sidx] : 0;
     unsigned long long npass = 0;
-    // row i in registers for pass 0: lane l holds samples 32 c + l
-    float ti[NW];
+    // sum_m t_i for pass 0 (padding samples included: st holds them)
     float Ti = 0.f;
 #pragma unroll
-    for (int c = 0; c < NW; ++c) {
-        ti[c] = c < v.Mw ? st[32 * c + lane] : 0.f;
-        Ti += ti[c];
-    }
+    for (int c = 0; c < NW; ++c) Ti += c < v.Mw ? st[32 * c + lane] : 0.f;
     Ti = warp_sum(Ti);
     const uint32_t ci = __ldg(v.xT + (int64_t)gx * 32 + lane);
     const uint32_t stage_bytes = (uint32_t)(v.Mp * 4 + 128);
@@ -646,7 +643,7 @@ __global__ void __launch_bounds__(512, 1) k_score_seg(IsingView v, WTable W, Sco
             const uint32_t cj = ((const uint32_t *)row)[v.Mp + lane];
             float su, sv;
             int dis;
-            pass0_consume<NW>(ti, Ti, ci, tj, cj, su, sv, dis);
+            pass0_consume<NW>(st, lane, Ti, ci, tj, cj, su, sv, dis);
             StageRows R{st, row, ci, cj, v.Mw, lane};
             float g, w;
             int passes = 0;

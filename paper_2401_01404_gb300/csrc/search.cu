@@ -1265,7 +1265,13 @@ static recon_status finish_results(recon_ctx *c, int64_t m, int64_t *count) {
     k_pair_keys<<<nblk(P), 256, 0, c->stream>>>(P, (int32_t *)S.res_pairs.p, (unsigned long long *)S.fk.p,
                                                 (uint32_t *)S.fv.p); note_launch();
     CKS(cudaGetLastError());
-    recon_status st = sort_kv(c, (unsigned long long *)S.fk.p, (uint32_t *)S.fv.p, P, 0, 64);
+    // by (i, j): both ids are below N, so only their low bits need passes (a
+    // stable LSD sort over j's bits, then over i's, orders by the full key)
+    int idb = 8;
+    while (idb < 32 && ((int64_t)1 << idb) < c->N) idb += 8;
+    recon_status st = sort_kv(c, (unsigned long long *)S.fk.p, (uint32_t *)S.fv.p, P, 0, idb);
+    if (st != RECON_OK) return st;
+    st = sort_kv(c, (unsigned long long *)S.fk.p, (uint32_t *)S.fv.p, P, 32, 32 + idb);
     if (st != RECON_OK) return st;
     GROW(S.fk2, sizeof(unsigned long long) * P);
     GROW(S.fv2, sizeof(uint32_t) * P);
