@@ -295,6 +295,7 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     c->bufs.resize(BUF_NSLOTS);
     if (const char *lim = getenv("RECON_FAULT_ALLOC_LIMIT")) c->alloc_limit = strtoull(lim, nullptr, 10);
     if (const char *st = getenv("RECON_FAULT_SCREEN_STALL")) c->fault_screen_stall = atoi(st) != 0;
+    if (const char *st = getenv("RECON_FAULT_SCORE_STALL")) c->fault_score_stall = atoi(st) != 0;
     c->model = model;
     c->device = dev;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);

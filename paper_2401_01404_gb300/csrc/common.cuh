@@ -222,6 +222,7 @@ struct GaussView {
 struct ScoreParams {
     float lambda, w_clamp, h_clamp;
     int grad_only;  // score by |d log pi / dW_ij| instead of the exact gain
+    int stall;      // fault injection: the segmented scorer issues no row copies
 };
 
 // |d log pi / dW_ij| from the smooth part's derivative D at the current W_ij = W0
@@ -298,13 +299,14 @@ struct recon_ctx {
     GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
     bool force_exact = false;  // exact gains even in gradient-distance mode (proposal targets)
     // host-side fault injection (tests): a cap on the device bytes the context
-    // may request (RECON_FAULT_ALLOC_LIMIT), and a screen whose loads are never
-    // issued, so that its bounded waits run out (RECON_FAULT_SCREEN_STALL)
+    // may request (RECON_FAULT_ALLOC_LIMIT), and a screen or a segmented scorer
+    // whose loads are never issued, so that its bounded waits run out
+    // (RECON_FAULT_SCREEN_STALL, RECON_FAULT_SCORE_STALL)
     uint64_t alloc_limit = 0, alloc_total = 0;
-    bool fault_screen_stall = false;
+    bool fault_screen_stall = false, fault_score_stall = false;
     ScoreParams sp() const {
         return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp,
-                           opt.distance == RECON_DIST_GRADIENT && !force_exact ? 1 : 0};
+                           opt.distance == RECON_DIST_GRADIENT && !force_exact ? 1 : 0, fault_score_stall ? 1 : 0};
     }
 };
 

@@ -603,6 +603,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
     const int mine = count > warp ? (count - warp + nw - 1) / nw : 0;  // candidates of this warp
     // lane 0: the warp's k-th candidate (chunk slot k - base) into stage k % SEG_RING
     auto issue = [&](int k, int base) {
+        if (p.stall) return;  // fault injection: the stage's wait runs out
         const int s = k % SEG_RING;
         const int g = cgj[k - base];
         mbar_expect_tx(bars + s, stage_bytes);
@@ -665,7 +666,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
         // the copies still in flight (issued within the chunk) land before the block can leave
         const int base = k / 32 * 32;
         const int nch = min(32, mine - base);
-        for (int kk = k; kk < base + nch && kk < k + SEG_RING; ++kk)
+        for (int kk = k; !p.stall && kk < base + nch && kk < k + SEG_RING; ++kk)
             seg_wait(bars + kk % SEG_RING, (uint32_t)((kk / SEG_RING) & 1));
     }
     if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);

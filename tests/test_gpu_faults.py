@@ -1,8 +1,8 @@
 """Failure handling, injected on the host (no GPU fault): a cap on the device
 memory a context may request makes the calls that need more fail with
-RECON_ENOMEM, and a tensor-core screen whose tile loads are never issued lets
-its bounded waits run out (about a second), so the launch ends with an error
-word and the call returns RECON_ETIMEOUT.  Afterwards the GPU is untouched: a
+RECON_ENOMEM, and a tensor-core screen (or a segmented scorer) whose loads are
+never issued lets its bounded waits run out (about a second), so the launch
+ends with an error word and the call returns RECON_ETIMEOUT.  Afterwards the GPU is untouched: a
 fresh context gives the exact result."""
 import os
 import time
@@ -77,5 +77,28 @@ def test_stalled_screen_times_out_and_the_gpu_stays_usable(R, data):
     assert e.value.status == R.RECON_ESTATE
     c.close()
     fresh = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    p1, d1 = fresh.best_pairs(16, 1.0)
+    assert np.array_equal(p0, p1) and np.array_equal(d0, d1)
+
+
+def test_stalled_scorer_times_out_and_the_gpu_stays_usable(R, data):
+    """The segmented scorer's row copies are never issued: each stage wait runs
+    out (about a second), the launch sets its error word and the search
+    returns RECON_ETIMEOUT; a fresh context gives the same result as before."""
+    Xs, lam = data
+    ex = R.RECON_KNN_EXHAUSTIVE  # every pair through the segmented scorer
+    ref = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=ex)
+    p0, d0 = ref.best_pairs(16, 1.0)
+    c = _with_env("RECON_FAULT_SCORE_STALL", "1", lambda: R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=ex))
+    t0 = time.perf_counter()
+    with pytest.raises(R.ReconError) as e:
+        c.best_pairs(16, 1.0)
+    assert e.value.status == R.RECON_ETIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    with pytest.raises(R.ReconError) as e:
+        c.best_pairs(16, 1.0)
+    assert e.value.status == R.RECON_ESTATE
+    c.close()
+    fresh = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=ex)
     p1, d1 = fresh.best_pairs(16, 1.0)
     assert np.array_equal(p0, p1) and np.array_equal(d0, d1)
