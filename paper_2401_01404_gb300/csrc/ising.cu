@@ -329,8 +329,7 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
     solve_from_pass0(R, Mp, su, sv, dis, Hsum, W0, lambda, wclamp, gain, wstar, passes);
 }
 
-// Row i staged in shared memory (t and the sign bits), row j streamed.
-// both rows in shared memory (row j in a staging buffer), the spins as the
+// Both rows in shared memory (row j in a staging buffer), the spins as the
 // lane's transposed bit columns: the Newton passes of a staged candidate touch
 // no global memory
 struct StageRows {
@@ -345,22 +344,6 @@ struct StageRows {
         b = tj[32 * c + lane];
         sa = (ci << (31 - c)) & 0x80000000u;
         sb_ = (cj << (31 - c)) & 0x80000000u;
-    }
-};
-
-struct SmemRows {
-    static constexpr int kNW = 0;
-    WARP_SUMS
-    const float *st;     // t_i, shared
-    const uint32_t *sb;  // x_i sign bits, shared
-    const float *Tj;
-    const uint32_t *Bj;
-    int Mw, lane;
-    __device__ __forceinline__ void get(int c, float &a, float &b, uint32_t &sa, uint32_t &sb_) const {
-        a = st[32 * c + lane];
-        b = __ldg(Tj + 32 * c + lane);
-        sa = (sb[c] << (31 - lane)) & 0x80000000u;
-        sb_ = (__ldg(Bj + c) << (31 - lane)) & 0x80000000u;
     }
 };
 
@@ -529,7 +512,7 @@ __global__ void k_objective(IsingView v, double *partials) {
 // covers node x = seg_node[s] (local id) and candidates at output positions
 // seg_start[s] .. + seg_count[s]; the second node of candidate q is
 // cand[2*pos + 1] when cand is given, else seg_vbase[s] + q.  Row x is staged
-// in shared memory once (and held in registers for pass 0).  Each warp takes
+// in shared memory once.  Each warp takes
 // its candidates in chunks of 32: the lanes first resolve the chunk's ids,
 // stored couplings and fields in parallel (one round of dependent loads per
 // chunk, not per pair), then lane 0 keeps SEG_RING candidate rows (t and the
