@@ -186,6 +186,9 @@ recon_status recon_score(recon_ctx *ctx, const int32_t *pairs, int64_t P, float 
  *           ascending d (ties by (i, j)).  d: cap floats (may be NULL).
  *   *m_out: the number written; when cap < m it is set to m and nothing is
  *           written (RECON_EINVAL).
+ * Errors besides RECON_EINVAL: RECON_ENOMEM (a search buffer or the device),
+ * RECON_ETIMEOUT when a bounded wait of the pair scorer (its staged row
+ * copies) or of the tensor-core screen ran out.
  * Synchronous. */
 recon_status recon_best_pairs(recon_ctx *ctx, int32_t k, double kappa, int32_t *pairs, float *d,
                               int64_t cap, int64_t *m_out, int32_t out_is_device);
