@@ -334,7 +334,13 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
 // no global memory
 struct StageRows {
     static constexpr int kNW = 0;
-    WARP_SUMS
+    // (pass 0 of a staged candidate is pass0_consume: only the Newton and gain
+    // passes sum through the row source)
+    __device__ __forceinline__ float sum(float a) const { return warp_sum(a); }
+    __device__ __forceinline__ void sum2(float &a, float &b) const {
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
     const float *st;  // t_i
     const float *tj;  // t_j
     uint32_t ci, cj;  // bit c: the spin of sample 32 c + lane (1: -1)
