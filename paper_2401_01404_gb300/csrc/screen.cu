@@ -8,24 +8,28 @@
 //   Ising:    F'(0) = g_ij = sum_m [r_i x_j + x_i r_j],  r = x - tanh(phi)
 //   Gaussian: a_ij = -sum_m [e_i x_j + x_i e_j],       e = x + s2 mu
 // i.e. G = [R | X] [X | R]^T, a product of two N x 2Mp matrices.  The screen
-// computes G with bf16 operands and f32 accumulation; its error is bounded per
-// pair (|dG_ij| <= 2^-8 (|R|_1,i + |R|_1,j) for the Ising model, whose spins
-// are exact in bf16, plus the accumulation error), so keeping every pair with
-// |G~_ij| > lambda - margin_ij loses none of the pairs with a nonzero gain.  The
-// survivors, and every stored coupling, are then scored exactly in FP32; the
-// m best of them are the exact m best pairs (the exhaustive base case of
-// Algorithm 3 over the whole node set).  The gradient as a cheap proxy for d is
-// the paper's own suggestion (App. B, "Gradient as distance").
+// computes G with bf16 operands (or, for the Ising model on request, E4M3) and
+// f32 accumulation; its error is bounded per pair: for the Ising model, whose
+// spins are exact in both types, |dG_ij| <= e_i + e_j with e_i the node's
+// actual rounding error sum_m |r~_im - r_im|, plus an accumulation allowance;
+// for the Gaussian model (2u + u^2) l_i l_j.  Keeping every pair with
+// |G~_ij| > lambda - margin_ij therefore loses none of the pairs with a nonzero
+// gain.  The survivors, and every stored coupling, are then scored exactly in
+// FP32; the m best of them are the exact m best pairs (the exhaustive base case
+// of Algorithm 3 over the whole node set).  The gradient as a cheap proxy for d
+// is the paper's own suggestion (App. B, "Gradient as distance").
 //
 // Kernel layout: a persistent grid; each CTA walks 128x256 units of G: the two
 // row halves of each 256x256 super-tile of the upper triangle (super-tiles in
-// bands of 8 super-rows, for L2 reuse).  Warp 4 issues TMA loads of 128x64 (A)
-// and 256x64 (B) bf16 tiles (128-byte swizzle) into a 4-stage ring, warp 5
-// issues tcgen05.mma (M=128, N=256, K=16) into one of two TMEM accumulators of
-// 256 columns, warps 0-3 drain the other
-// accumulator (tcgen05.ld, one TMEM lane = one row per thread) and append the
-// surviving pairs.  Every wait is bounded (1 s); on a timeout the kernel sets
-// an error word, lets its own copies land, frees TMEM and returns.
+// bands of 8 super-rows, for L2 reuse).  Warp 8 issues TMA loads of 128-row (A)
+// and 256-row (B) tiles of 128-byte k-block rows (64 bf16 or 128 E4M3; 128-byte
+// swizzle) into a 4-stage ring, warp 9 issues tcgen05.mma (M=128, N=256, K=16
+// bf16 / 32 E4M3) into one of two TMEM accumulators of 256 columns, and warps
+// 0-7 drain the other accumulator (tcgen05.ld; warp w reads TMEM lanes
+// 32 (w % 4) .. + 31, one row per thread, and columns 128 (w / 4) .. + 127)
+// and stage the surviving pairs.  Every wait is bounded (1 s); on a timeout
+// the kernel sets an error word, lets its own copies land, frees TMEM and
+// returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
