@@ -15,9 +15,14 @@
 // bracket.  F is evaluated as delta*F'(0) plus per-sample remainders that are
 // O(delta^2), never as a difference of two large sums.
 //
-// Thread mapping: one warp per pair; lane l holds samples 32c + l.  Rows of up
-// to 1024 samples live in registers for the whole solve; longer rows are
-// re-read from L1/L2 on every pass.
+// Thread mapping: lane l of a warp holds samples 32c + l.  The pair scorer
+// (k_score) gives each pair a warp with both rows in registers (up to 1024
+// samples; longer rows are re-read from L1/L2 on every pass).  The segmented
+// scorer (k_score_seg) gives each node's candidate list a block: row i in shared
+// memory, candidate rows brought into per-warp shared-memory stages by bulk
+// asynchronous copies.  A wide matching batch of updates (k_update_blk) gives
+// each pair a block whose warps split the samples (BlockRows); runs of thin
+// batches (k_update_rounds) give each pair a warp.
 #include "common.cuh"
 
 namespace {
