@@ -346,6 +346,77 @@ def test_gauss_diagonal_closed_form(oracle):
     assert np.allclose(o.s2, u, rtol=1e-11)
 
 
+def _gauss_problem(N=13, M=80, seed=51):
+    """Samples of a sparse Gaussian precision model (dense Cholesky sampler)."""
+    W = _rand_W(N, seed, p=0.3, scale=0.3)
+    np.fill_diagonal(W, np.abs(W).sum(1) + 1.0)
+    X = inputs.gaussian_dense_samples(W, M, seed + 1)
+    return X, 2.0 * math.sqrt(M)
+
+
+def test_gauss_update_reports_the_objective_increase(oracle):
+    """One coupling update (App. A's tracked sums mu_i += dW x_j, mu_j += dW x_i)
+    raises the objective by exactly the gain the score reports, measured against
+    an objective whose neighbour sums are rebuilt from W from scratch; the
+    tracked sums equal W x afterwards."""
+    X, lam = _gauss_problem()
+    N = X.shape[0]
+    o = oracle.GaussOracle(X, lam=0.25 * lam)
+    rng = np.random.default_rng(52)
+    moved = 0
+    for _ in range(40):
+        a, b = sorted(rng.choice(N, 2, replace=False))
+        gain, wst = o.score([[a, b]])
+        before = o.objective()
+        o.update([[a, b]])
+        assert o.W[a, b] == pytest.approx(wst[0], rel=1e-9, abs=1e-12) and o.W[b, a] == o.W[a, b]
+        mu_tracked = o.mu.copy()
+        o.set_state(o.W, o.s2)  # mu rebuilt from W
+        assert np.allclose(mu_tracked, o.mu, rtol=1e-10, atol=1e-10)
+        after = o.objective()
+        assert after - before == pytest.approx(gain[0], rel=1e-8, abs=1e-9 * abs(before))
+        assert after >= before - 1e-9 * abs(before)
+        moved += abs(wst[0]) > 0
+        if _ % 7 == 6:
+            o.diag_sweep()
+    assert moved >= 10
+    Wo = o.W - np.diag(np.diag(o.W))
+    assert np.allclose(o.mu, Wo @ X, rtol=1e-10, atol=1e-10)
+
+
+def test_gauss_single_updates_never_decrease_objective(oracle):
+    X, lam = _gauss_problem(seed=53)
+    o = oracle.GaussOracle(X, lam=lam)
+    prev = o.objective()
+    rng = np.random.default_rng(54)
+    for _ in range(60):
+        a, b = sorted(rng.choice(o.N, 2, replace=False))
+        o.update([[a, b]])
+        cur = o.objective()
+        assert cur >= prev - 1e-12 * abs(prev)
+        prev = cur
+    o.diag_sweep()
+    assert o.objective() >= prev - 1e-12 * abs(prev)
+
+
+def test_gauss_gcd_and_cd_reach_the_same_optimum(oracle):
+    """The Gaussian pseudo-likelihood with the Laplace prior is convex in W for
+    fixed diagonal and the joint sweep converges: CD (Algorithm 1) and GCD
+    (Algorithm 2, kappa = 1) end at the same optimum."""
+    X, lam = _gauss_problem(N=14, M=120, seed=55)
+    a = oracle.GaussOracle(X, lam=lam)
+    b = oracle.GaussOracle(X, lam=lam)
+    ha = oracle.cd(a, eps=1e-11, max_iters=3000)
+    hb = oracle.gcd(b, kappa=1.0, eps=1e-11, max_iters=20000)
+    assert ha[-1][1] < 1e-11 and hb[-1][1] < 1e-11
+    assert a.objective() == pytest.approx(b.objective(), rel=1e-8)
+    assert np.allclose(a.W, b.W, atol=1e-5)
+    assert np.allclose(a.s2, b.s2, rtol=1e-5)
+    # at the optimum every single-coupling gain is zero
+    g, _ = a.score(oracle.all_pairs(np.arange(a.N)))
+    assert g.max() <= 1e-8 * abs(a.objective())
+
+
 # ---------------------------------------------------------------- searches
 
 
