@@ -167,7 +167,10 @@ def _exact_top(o, m, N):
     return pairs[order[:m]], g[order[:m]], pairs, g
 
 
-@pytest.mark.parametrize("N,M,m", [(100, 200, 100), (64, 500, 300), (90, 128, 20)])
+@pytest.mark.parametrize("N,M,m", [(100, 200, 100), (64, 500, 300), (90, 128, 20),
+                                   # 32-word rows: the segmented scorer's widest instantiation,
+                                   # including a ragged last word (993, 600) and a full one (1024)
+                                   (160, 600, 150), (150, 1000, 120), (130, 1024, 100), (140, 993, 200)])
 def test_exhaustive_best_matches_oracle(R, oracle, N, M, m):
     X = _wl(N, M, seed=41 + m)
     lam = inputs.default_lambda(N, M, 0.5)
@@ -221,6 +224,30 @@ def test_findbest_nndescent_recall(R, oracle):
     assert rec >= 0.9, rec
     st = ctx.stats()
     assert st["knn_iters"] >= 1 and st["level_k"][0] >= 10
+
+
+def test_knn_lists_at_full_size_match_oracle(R, oracle):
+    """N=2000, M=1000 (32-word rows): every entry of the first level's k-NN
+    lists, whose d the segmented scorer computed inside the NNDescent search
+    (launch configuration of the benchmark), against the FP64 oracle at the
+    W = 0 start, pair by pair; the lists are ascending, distinct and self-free."""
+    wl = inputs.config("ising_n2000_m1000", device="cuda")
+    lam = inputs.default_lambda(wl.N, wl.M)
+    ctx = R.Recon(wl.samples_major(), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_NNDESCENT)
+    ctx.best_pairs(16, 2.0)
+    ids, d = ctx.knn_graph()
+    assert ids.shape == (wl.N, 16)
+    assert np.all(ids >= 0) and np.all(ids != np.arange(wl.N)[:, None])
+    assert all(len(set(r)) == len(r) for r in ids.tolist())
+    assert np.all(np.diff(d, axis=1) >= 0)
+    pairs = np.stack([np.repeat(np.arange(wl.N), 16), ids.ravel()], 1).astype(np.int32)
+    h = oracle.ising_fields_at_zero(wl.X)
+    phi = np.repeat(h[:, None], wl.M, 1)
+    g_ref, _ = oracle.ising_score_rows(wl.X, phi, pairs, lam)
+    assert_gains(-d.ravel(), g_ref)
+    assert (g_ref > 0).sum() >= wl.N  # the lists hold the planted neighbours, not only zero gains
+    st = ctx.stats()
+    assert st["knn_iters"] >= 2
 
 
 def test_invalid_inputs_are_rejected(R):
