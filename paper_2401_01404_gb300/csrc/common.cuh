@@ -303,6 +303,9 @@ struct recon_ctx {
     // whose loads are never issued, so that its bounded waits run out
     // (RECON_FAULT_SCREEN_STALL, RECON_FAULT_SCORE_STALL)
     uint64_t alloc_limit = 0, alloc_total = 0;
+    // Newton passes counted by calls that keep their counters outside c->cnt
+    // (recon_score_noalloc's static words)
+    int64_t newton_extra = 0;
     bool fault_screen_stall = false, fault_score_stall = false;
     ScoreParams sp() const {
         return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp,
@@ -418,10 +421,15 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
 // general form: operands of K columns (a multiple of 64 bf16 or 128 fp8), of which the first
 // k_valid are nonzero; threshold `thr` on |G_ij|, margin rel * (l_i + l_j) (or l_i l_j) + abs_margin
 // when l1 is given, stored couplings skipped when skip_stored
+// r1 != NULL: the rank-one form at the empty network (A = B the E4M3 spin rows, r1 the
+// per-node (s_i, tau_i); keep |2 S_ij - tau_j s_i - tau_i s_j| > thr - abs_margin)
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
                              unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
-                             int k_valid);
+                             int k_valid, const float2 *r1);
+int screen_k_rank1(recon_ctx *c);
+float screen_rank1_margin(recon_ctx *c);
+cudaError_t launch_screen_prep_rank1(recon_ctx *c, void *A, float2 *r1, unsigned long long *flag);
 
 // host helpers (api.cu)
 recon_status set_err(recon_ctx *c, recon_status st, const char *fmt, ...);

@@ -19,6 +19,17 @@
 // of Algorithm 3 over the whole node set).  The gradient as a cheap proxy for d
 // is the paper's own suggestion (App. B, "Gradient as distance").
 //
+// The empty network (W = 0, where Algorithm 2 starts).  Every sample of node i
+// then has the same field, so t_im = tau_i for m < M and, with s_i = sum_m x_im,
+//   g_ij = 2 sum_m x_im x_jm - tau_j s_i - tau_i s_j :
+// G is the spin product X X^T (K = M instead of 2M) plus a rank-two correction
+// applied in the epilogue.  The spins are exact in E4M3 and every partial sum of
+// the product is an integer of magnitude <= M, so the tensor-core product is
+// exact whatever the accumulator's width; the only error left is the FP32
+// rounding of the correction, covered by a margin of Mp / 2048 (several hundred
+// times that rounding, and also above the FP32 rounding of the exact scorer's
+// own first pass, so that no pair the scorer gives a nonzero gain is dropped).
+//
 // Kernel layout: a persistent grid; each CTA walks 128x256 units of G: the two
 // row halves of each 256x256 super-tile of the upper triangle (super-tiles in
 // bands of 8 super-rows, for L2 reuse).  Warp 8 issues TMA loads of 128-row (A)
@@ -210,6 +221,7 @@ struct ScreenArgs {
     float abs_margin;   // plus this much
     int product_margin; // margin rel_err * l_i * l_j (Gaussian) instead of rel_err * (l_i + l_j)
     const float *l1;    // per-node norms of the margin
+    const float2 *r1;   // rank-one form: per node (s_i, tau_i)
     WTable W;           // pairs with a stored coupling are left to the caller
     int skip_stored;    // leave out pairs that hold a stored coupling
     int32_t *out;       // survivors (i, j), i < j
@@ -219,7 +231,7 @@ struct ScreenArgs {
     int stall;          // fault injection: issue no loads, so the bounded waits run out
 };
 
-template <bool F8>
+template <bool F8, bool R1>
 __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
                                                        const __grid_constant__ CUtensorMap tB, ScreenArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -286,7 +298,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             const uint32_t ab = F8 ? 0u : 1u;
             const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
-            int64_t kb_all = 0, it = 0;
+            int64_t kb_all = 0, it = 0, last_it = -1;  // last_it: the unit of the last accumulator commit
             for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x, ++it) {
                 const int b = (int)(it & 1);
                 if (!mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
@@ -320,15 +332,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     mma_commit(empty + s);
                 }
                 mma_commit(acc_full + b);
+                last_it = it;
                 if (!ok) break;
+            }
+            // after an abort, the MMAs already issued may still be reading the stages and
+            // writing TMEM: wait (bounded) for the last commit, which tracks all of them,
+            // before the CTA frees TMEM and leaves
+            if (last_it >= 0 && *(volatile int *)abort) {
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(acc_full + (last_it & 1), (uint32_t)((last_it >> 1) & 1)))
+                    if (gtimer() - t0 > 1000000000ull) break;
             }
         }
     } else {  // epilogue warps: row 32 (warp % 4) + lane, columns 128 (warp / 4) .. + 127 of each unit
         const int rg = warp & 3, ch = warp >> 2;
-        // per-warp copy of its 128 column norms (the margin's l_j), read as
-        // 128-bit broadcasts
-        float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * (BN / 2);
-        int2 *sbuf = (int2 *)(smem + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * (BN / 2) * sizeof(float)) +
+        // per-warp copy of its 128 column norms (the margin's l_j), or in the
+        // rank-one form of its columns' s_j (first 128) and tau_j (next 128), read
+        // as 128-bit broadcasts
+        float *cn = (float *)(smem + STAGES * (A_BYTES + B_BYTES) + 256) + warp * BN;
+        int2 *sbuf = (int2 *)(smem + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * BN * sizeof(float)) +
                      warp * SBUF;
         int nbuf = 0;  // warp-uniform fill of sbuf
         // write the staged survivors: each lane checks up to SBUF / 32 entries against
@@ -372,9 +394,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         // the column norms l_j of a unit: lane holds columns 4 lane .. 4 lane + 3 of
         // the warp's half, loaded one unit ahead so that their latency hides
         // behind the compare
-        auto load_norms = [&](int jt, float4 &n0) {
+        // (rank-one form: n0 = s_j and n1 = tau_j of the four columns)
+        auto load_norms = [&](int jt, float4 &n0, float4 &n1) {
             const int j = jt + (BN / 2) * ch + 4 * lane;
-            if (a.l1 && j + 3 < a.n) {
+            if constexpr (R1) {
+                if (j + 3 < a.n) {
+                    const float4 p0 = *(const float4 *)(a.r1 + j), p1 = *(const float4 *)(a.r1 + j + 2);
+                    n0 = make_float4(p0.x, p0.z, p1.x, p1.z);
+                    n1 = make_float4(p0.y, p0.w, p1.y, p1.w);
+                } else {
+                    float q[4], w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 e = j + u < a.n ? a.r1[j + u] : make_float2(0.f, 0.f);
+                        q[u] = e.x;
+                        w[u] = e.y;
+                    }
+                    n0 = make_float4(q[0], q[1], q[2], q[3]);
+                    n1 = make_float4(w[0], w[1], w[2], w[3]);
+                }
+            } else if (a.l1 && j + 3 < a.n) {
                 n0 = *(const float4 *)(a.l1 + j);
             } else {
                 float q[4];
@@ -383,16 +422,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 n0 = make_float4(q[0], q[1], q[2], q[3]);
             }
         };
+        // the row's l_i, or in the rank-one form its (s_i, tau_i)
         auto load_row = [&](int ra_) {
             const int i_ = ra_ + 32 * rg + lane;
-            return (a.l1 && i_ < a.n) ? a.l1[i_] : 0.f;
+            if constexpr (R1) return i_ < a.n ? a.r1[i_] : make_float2(0.f, 0.f);
+            else return make_float2((a.l1 && i_ < a.n) ? a.l1[i_] : 0.f, 0.f);
         };
         int ra = 0, jt = 0;
-        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        float li_n = 0.f;
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        float2 li_n = make_float2(0.f, 0.f);
         if ((int64_t)blockIdx.x < a.ntiles) {
             walk.map(blockIdx.x, ra, jt);
-            load_norms(jt, n0);
+            load_norms(jt, n0, n1);
             li_n = load_row(ra);
         }
         int64_t it = 0;
@@ -403,20 +444,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             // keep iff |g| > lambda - margin, written |g| + s c_j > thr:
             //   sum margin     rel (l_i + l_j):  c_j = rel l_j, s = 1,        thr = lambda - rel l_i
             //   product margin rel l_i l_j:      c_j = l_j,     s = rel l_i,  thr = lambda
-            const float li = li_n;
-            const float sc = a.product_margin ? a.rel_err * li : 1.f;
-            const float thr = (a.product_margin ? a.lambda : a.lambda - a.rel_err * li) - a.abs_margin;
-            const float f = a.product_margin ? 1.f : a.rel_err;
-            const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
-            ((float4 *)cn)[lane] = c0;
-            // the warp's largest c_j in one reduction: c_j >= +0, whose bit patterns
-            // order like the values
-            const float cmax = __uint_as_float(
-                __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w)))));
+            // rank-one form: g = 2 S_ij - (tau_j s_i + tau_i s_j), thr = lambda - abs_margin,
+            //   and |tau_j s_i + tau_i s_j| <= cb = |s_i| max |tau_j| + |tau_i| max |s_j|
+            const float li = li_n.x;
+            float sc, thr, cmax, thr_q;  // thr_q: the unit-level test's threshold
+            if constexpr (R1) {
+                ((float4 *)cn)[lane] = n0;
+                ((float4 *)(cn + BN / 2))[lane] = n1;
+                // abs values order like their bit patterns: one reduction each
+                const float umax = __uint_as_float(__reduce_max_sync(
+                    0xffffffffu, __float_as_uint(fmaxf(fmaxf(fabsf(n0.x), fabsf(n0.y)), fmaxf(fabsf(n0.z), fabsf(n0.w))))));
+                const float vmax = __uint_as_float(__reduce_max_sync(
+                    0xffffffffu, __float_as_uint(fmaxf(fmaxf(fabsf(n1.x), fabsf(n1.y)), fmaxf(fabsf(n1.z), fabsf(n1.w))))));
+                sc = 1.f;
+                cmax = fabsf(li) * vmax + fabsf(li_n.y) * umax;
+                thr = a.lambda - a.abs_margin;
+                // the unit-level test is a bound with its own FP32 roundings (a few
+                // units of 2^-24 of 4 Mp): a sixteenth of the margin absorbs them
+                thr_q = thr - 0.0625f * a.abs_margin;
+            } else {
+                sc = a.product_margin ? a.rel_err * li : 1.f;
+                thr = (a.product_margin ? a.lambda : a.lambda - a.rel_err * li) - a.abs_margin;
+                const float f = a.product_margin ? 1.f : a.rel_err;
+                const float4 c0 = make_float4(f * n0.x, f * n0.y, f * n0.z, f * n0.w);
+                ((float4 *)cn)[lane] = c0;
+                // the warp's largest c_j in one reduction: c_j >= +0, whose bit patterns
+                // order like the values
+                cmax = __uint_as_float(
+                    __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fmaxf(c0.x, c0.y), fmaxf(c0.z, c0.w)))));
+                thr_q = thr;
+            }
+            const float ui = li, vi = li_n.y;
             // the next unit's mapping and norms, in flight during this unit's compare
             if (t + gridDim.x < a.ntiles) {
                 walk.map(t + gridDim.x, ra, jt);
-                load_norms(jt, n0);
+                load_norms(jt, n0, n1);
                 li_n = load_row(ra);
             }
             __syncwarp();
@@ -445,20 +507,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                                       fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
                 unsigned long long mk = 0;
                 const int j0 = jt_cur + 64 * hf;
-                if (m + sc * cmax > thr) {
+                if ((R1 ? 2.f * m : m) + sc * cmax > thr_q) {
                     // exact test of the 64 columns as a bit mask (branch-free), then
                     // j > i, j < n and the stored couplings, then one reservation
                     const float4 *c4p = (const float4 *)(cn + 64 * hf);
                     // two 32-bit halves, four partial masks each: short dependency chains
                     uint32_t mw[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+                    if constexpr (R1) {
+                        const float4 *v4p = (const float4 *)(cn + BN / 2 + 64 * hf);
 #pragma unroll
-                    for (int q4 = 0; q4 < 16; ++q4) {
-                        const float4 c4 = c4p[q4];
-                        const int h = q4 >> 3, sh = 4 * (q4 & 7);
-                        mw[h][0] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr) << (sh + 0);
-                        mw[h][1] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr) << (sh + 1);
-                        mw[h][2] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr) << (sh + 2);
-                        mw[h][3] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr) << (sh + 3);
+                        for (int q4 = 0; q4 < 16; ++q4) {
+                            const float4 u4 = c4p[q4], v4 = v4p[q4];
+                            const int h = q4 >> 3, sh = 4 * (q4 & 7);
+                            // g = 2 S - (tau_j s_i + tau_i s_j)
+#define R1_BIT(k, uu, vv)                                                                                       \
+    mw[h][k] |= (uint32_t)(fabsf(fmaf(2.f, __uint_as_float(r[4 * q4 + k]), -fmaf(vv, ui, vi * uu))) > thr)      \
+                << (sh + k)
+                            R1_BIT(0, u4.x, v4.x);
+                            R1_BIT(1, u4.y, v4.y);
+                            R1_BIT(2, u4.z, v4.z);
+                            R1_BIT(3, u4.w, v4.w);
+#undef R1_BIT
+                        }
+                    } else {
+#pragma unroll
+                        for (int q4 = 0; q4 < 16; ++q4) {
+                            const float4 c4 = c4p[q4];
+                            const int h = q4 >> 3, sh = 4 * (q4 & 7);
+                            mw[h][0] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 0])) + sc * c4.x > thr) << (sh + 0);
+                            mw[h][1] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 1])) + sc * c4.y > thr) << (sh + 1);
+                            mw[h][2] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 2])) + sc * c4.z > thr) << (sh + 2);
+                            mw[h][3] |= (uint32_t)(fabsf(__uint_as_float(r[4 * q4 + 3])) + sc * c4.w > thr) << (sh + 3);
+                        }
                     }
                     mk = (unsigned long long)((mw[0][0] | mw[0][1]) | (mw[0][2] | mw[0][3])) |
                          ((unsigned long long)((mw[1][0] | mw[1][1]) | (mw[1][2] | mw[1][3])) << 32);
@@ -606,6 +686,35 @@ __global__ void k_prep_ising_fp8(IsingView v, int K8, uint8_t *A, uint8_t *B, fl
     if (lane == 0) q[i] = (e + acc * s) * (1.f + 1.f / 1024.f);
 }
 
+// Operands of the rank-one form at the empty network: E4M3 spin rows (+-1 for
+// the M samples, zero past them, K8 = Mp rounded up to 128 entries) and per node
+// (s_i, tau_i) with s_i = sum_m x_im (exact) and tau_i = t_i of its first sample.
+// A node whose t differs between its samples sets *flag (the caller then uses
+// the general form).
+__global__ void k_prep_ising_rank1(IsingView v, int K8, uint8_t *A, float2 *r1, unsigned long long *flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= v.N) return;
+    const float tau = v.t[i * v.Mp];
+    int s = 0;
+    bool same = true;
+    for (int m = lane; m < K8; m += 32) {
+        float x = 0.f;
+        if (m < v.M) {
+            x = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? -1.f : 1.f;
+            same &= v.t[i * v.Mp + m] == tau;
+        }
+        A[i * K8 + m] = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+        s += (int)x;
+    }
+    s = warp_sum_i(s);
+    const bool all_same = __all_sync(0xffffffffu, same);
+    if (lane == 0) {
+        r1[i] = make_float2((float)s, tau);
+        if (!all_same) atomicOr(flag, 1ull);
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
@@ -614,6 +723,20 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 int screen_k(recon_ctx *c, bool fp8) {
     const int k = 2 * (int)c->Mp;
     return fp8 ? (k + BK8 - 1) / BK8 * BK8 : k;
+}
+
+// operand row length of the rank-one form: Mp E4M3 entries padded to 128
+int screen_k_rank1(recon_ctx *c) { return ((int)c->Mp + BK8 - 1) / BK8 * BK8; }
+
+// the margin of the rank-one form (see the header)
+float screen_rank1_margin(recon_ctx *c) { return (float)c->Mp / 2048.f; }
+
+cudaError_t launch_screen_prep_rank1(recon_ctx *c, void *A, float2 *r1, unsigned long long *flag) {
+    if (c->model != RECON_ISING) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)((c->N * 32 + 255) / 256);
+    k_prep_ising_rank1<<<grid, 256, 0, c->stream>>>(c->iv(), screen_k_rank1(c), (uint8_t *)A, r1, flag);
+    note_launch();
+    return cudaGetLastError();
 }
 
 // bf16 (or, for the Ising model, fp8) operand rows and the margin's norms
@@ -664,7 +787,8 @@ float screen_acc_err(recon_ctx *c, bool fp8) {
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
                              unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
-                             int k_valid) {
+                             int k_valid, const float2 *r1) {
+    if (r1 && !fp8) return cudaErrorInvalidValue;  // the rank-one form reads E4M3 spins
     const int bke = fp8 ? BK8 : BK;  // elements per 128-byte k-block row
     const int kchunk = fp8 ? 32 : 16;  // elements per MMA
     if (K % bke || k_valid <= K - bke || k_valid > K || k_valid % kchunk) return cudaErrorInvalidValue;
@@ -688,14 +812,17 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * (BN / 2) * sizeof(float) +
+    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * BN * sizeof(float) +
                         EPI_WARPS * SBUF * sizeof(int2);
-    static int attr_device[2] = {-1, -1};  // per device and variant; set once for each
-    if (attr_device[fp8] != c->device) {
-        cudaError_t e = fp8 ? cudaFuncSetAttribute(k_screen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(k_screen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int attr_device[3] = {-1, -1, -1};  // per device and variant; set once for each
+    const int variant = r1 ? 2 : fp8 ? 1 : 0;
+    if (attr_device[variant] != c->device) {
+        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = variant == 2   ? cudaFuncSetAttribute(k_screen<true, true>, at, (int)smem)
+                        : variant == 1 ? cudaFuncSetAttribute(k_screen<true, false>, at, (int)smem)
+                                       : cudaFuncSetAttribute(k_screen<false, false>, at, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_device[fp8] = c->device;
+        attr_device[variant] = c->device;
     }
     ScreenArgs a;
     a.n = (int)c->N;
@@ -708,6 +835,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.abs_margin = abs_margin;
     a.product_margin = product_margin;
     a.l1 = l1;
+    a.r1 = r1;
     a.W = c->W;
     a.skip_stored = skip_stored ? 1 : 0;
     a.out = out;
@@ -716,10 +844,13 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
     const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);  // persistent: one CTA per SM
-    if (fp8)
-        k_screen<true><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+    const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
+    if (r1)
+        k_screen<true, true><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
+    else if (fp8)
+        k_screen<true, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
     else
-        k_screen<false><<<(unsigned)std::max<int64_t>(grid, 1), THREADS, smem, c->stream>>>(ta, tb, a);
+        k_screen<false, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();
     if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.ntiles;
     return cudaGetLastError();
@@ -729,5 +860,5 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
                           unsigned long long *count, float margin_scale, double *flop_out, bool fp8) {
     return launch_screen_ex(c, A, B, screen_k(c, fp8), (float)c->opt.lambda, l1, margin_scale,
                             c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out, fp8, 0.f,
-                            2 * (int)c->Mp);
+                            2 * (int)c->Mp, nullptr);
 }

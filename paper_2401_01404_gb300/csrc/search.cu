@@ -1455,12 +1455,7 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
     S.res_n = 0;
     S.g0_K = 0;
     const bool fp8 = c->opt.screen_fp8 != 0;
-    const int64_t N = c->N, K = screen_k(c, fp8);
-    const size_t esz = fp8 ? 1 : sizeof(uint16_t);
-    GROW(S.scr_A, esz * (size_t)N * K);
-    GROW(S.scr_B, esz * (size_t)N * K);
-    GROW(S.scr_l1, sizeof(float) * N);
-    CKS(launch_screen_prep(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, fp8));
+    const int64_t N = c->N;
     int64_t nnz = 0;
     {
         CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH0), 0, sizeof(unsigned long long), c->stream));
@@ -1469,6 +1464,28 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
         recon_status st = read_counter(c, CNT_SCRATCH0, &v);
         if (st != RECON_OK) return st;
         nnz = (int64_t)v;
+    }
+    // the empty network (no stored coupling): every sample of a node has the same
+    // field, and the screen takes its exact rank-one form (E4M3 spins, K = Mp);
+    // the prep kernel confirms the constant rows, else the general form runs
+    bool rank1 = c->model == RECON_ISING && nnz == 0 && !c->opt.screen_no_rank1;
+    if (rank1) {
+        GROW(S.scr_A, (size_t)N * screen_k_rank1(c));
+        GROW(S.scr_l1, sizeof(float2) * N);
+        CKS(cudaMemsetAsync(counter(c, CNT_SCRATCH2), 0, sizeof(unsigned long long), c->stream));
+        CKS(launch_screen_prep_rank1(c, S.scr_A.p, (float2 *)S.scr_l1.p, counter(c, CNT_SCRATCH2)));
+        unsigned long long nonconst = 0;
+        recon_status st = read_counter(c, CNT_SCRATCH2, &nonconst);
+        if (st != RECON_OK) return st;
+        rank1 = nonconst == 0;
+    }
+    if (!rank1) {
+        const int64_t K = screen_k(c, fp8);
+        const size_t esz = fp8 ? 1 : sizeof(uint16_t);
+        GROW(S.scr_A, esz * (size_t)N * K);
+        GROW(S.scr_B, esz * (size_t)N * K);
+        GROW(S.scr_l1, sizeof(float) * N);
+        CKS(launch_screen_prep(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, fp8));
     }
     int64_t cap = std::max<int64_t>(int64_t(1) << 20, 16 * m);
     const float rel = screen_rel_err(c->model, (int)c->Mp, fp8);
@@ -1488,8 +1505,14 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
             CKS(cudaEventRecord(ea, c->stream));
         }
         double flop = 0.0;
-        CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
-                          counter(c, CNT_SCRATCH1), rel, &flop, fp8));
+        if (rank1)
+            CKS(launch_screen_ex(c, S.scr_A.p, S.scr_A.p, screen_k_rank1(c), (float)c->opt.lambda, nullptr, 0.f, 0,
+                                 true, (int32_t *)S.cand.p, cap, counter(c, CNT_SCRATCH1), &flop, true,
+                                 screen_rank1_margin(c), (int)c->Mp, (const float2 *)S.scr_l1.p));
+        else
+            CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
+                              counter(c, CNT_SCRATCH1), rel, &flop, fp8));
+        if (rank1) c->stats.screen_rank1 += 1;
         if (c->opt.timing) {
             CKS(cudaEventRecord(eb, c->stream));
             c->timed.push_back({ea, eb, -1});

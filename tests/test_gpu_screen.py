@@ -2,8 +2,10 @@
 the exact best pairs — the screen only discards pairs whose gain is provably
 zero, and the survivors are scored exactly.  Checked against the oracle and
 against the CUDA-core exhaustive search, element by element, on sizes with
-ragged tiles (N not a multiple of 128, M not a multiple of 64).  The same
-for the FP8 (E4M3) operands, whose wider margin keeps the result exact."""
+ragged tiles (N not a multiple of 128, M not a multiple of 64).  Three forms:
+the general one with bf16 operands, the same with FP8 (E4M3) operands (a wider
+margin keeps it exact), and the rank-one form of the empty network (E4M3 spin
+product, exact; the library's default whenever no coupling is stored)."""
 import math
 
 import numpy as np
@@ -37,14 +39,29 @@ def _wl(N, M, seed):
     return inputs.gibbs_ising(N, edges, w, h, M, 150, seed)
 
 
+# screen forms: options of each (the general forms are forced off the rank-one path)
+FORMS = {"bf16": dict(screen_fp8=0, screen_no_rank1=1), "fp8": dict(screen_fp8=1, screen_no_rank1=1),
+         "rank1": dict(screen_fp8=0, screen_no_rank1=0)}
+
+
+def _grad_at_zero(X, oracle):
+    """F'(0) of every pair at the W = 0 start: sum_m [x_j (x_i - t_i) + x_i (x_j - t_j)]
+    with t_i = tanh(h_i) and h the oracle's fitted fields."""
+    t = np.tanh(oracle.ising_fields_at_zero(X))
+    Xf = X.astype(np.float64)
+    s = Xf.sum(1)
+    return 2.0 * Xf @ Xf.T - np.outer(s, t) - np.outer(t, s)
+
+
 def _close(g_gpu, g_ref):
     tol = REL * np.abs(g_ref) + FLOOR * max(float(np.max(g_ref)), 1e-30)
     return np.abs(np.asarray(g_gpu, dtype=np.float64) - g_ref) <= tol
 
 
-@pytest.mark.parametrize("fp8", [0, 1])
-@pytest.mark.parametrize("N,M,c", [(100, 200, 1.0), (300, 130, 0.5), (257, 1000, 1.0), (129, 37, 0.7)])
-def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c, fp8):
+@pytest.mark.parametrize("form", ["bf16", "fp8", "rank1"])
+@pytest.mark.parametrize("N,M,c", [(100, 200, 1.0), (300, 130, 0.5), (257, 1000, 1.0), (129, 37, 0.7),
+                                   (200, 256, 1.0), (140, 1024, 1.0)])
+def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c, form):
     X = _wl(N, M, 100 + N)
     lam = inputs.default_lambda(N, M, c)
     o = oracle.IsingOracle(X, lam)
@@ -52,7 +69,7 @@ def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c, fp8):
     g_ref, _ = o.score(allp)
     npos = int((g_ref > 1e-6 * g_ref.max()).sum())
     scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1,
-                  screen_fp8=fp8)
+                  **FORMS[form])
     kappa = (len(allp) + 0.4) / N  # ask for every pair: the screen returns exactly its survivors
     p, d = scr.best_pairs(4, kappa)
     found = {tuple(x) for x in p.tolist()}
@@ -60,19 +77,28 @@ def test_screen_keeps_every_pair_with_a_gain(R, oracle, N, M, c, fp8):
     assert pos <= found, len(pos - found)
     st = scr.stats()
     assert st["screen_launches"] == 1 and st["screen_survivors"] == len(p)
-    if not fp8:
+    assert st["screen_rank1"] == (1 if form == "rank1" else 0)
+    if form != "fp8":
         assert len(p) < len(allp) or npos > len(allp) // 2  # the screen discarded pairs
+    if form == "rank1":
+        # the rank-one form is exact up to its small margin (Mp / 2048): its survivors
+        # are the pairs with |F'(0)| above lambda minus that margin, and no others
+        G = _grad_at_zero(X, oracle)[allp[:, 0], allp[:, 1]]
+        mp = 32 * ((M + 31) // 32)
+        must = int((np.abs(G) > lam + 1e-3).sum())
+        may = int((np.abs(G) > lam - mp / 2048.0 - 1e-3).sum())
+        assert must <= len(p) <= may, (must, len(p), may)
     gd = dict(zip(map(tuple, allp.tolist()), g_ref))
     assert _close(-d, np.array([gd[x] for x in map(tuple, p.tolist())])).all()
 
 
-@pytest.mark.parametrize("fp8", [0, 1])
+@pytest.mark.parametrize("form", ["bf16", "fp8", "rank1"])
 @pytest.mark.parametrize("N,M,kappa", [(200, 300, 1.0), (500, 500, 2.0), (1100, 250, 1.0)])
-def test_screen_best_equals_exhaustive(R, N, M, kappa, fp8):
+def test_screen_best_equals_exhaustive(R, N, M, kappa, form):
     X = _wl(N, M, 200 + N)
     lam = inputs.default_lambda(N, M)
     Xs = np.ascontiguousarray(X.T)
-    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
+    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, **FORMS[form])
     ex = R.Recon(Xs, R.RECON_ISING, lam=lam)
     m = int(math.floor(kappa * N + 0.5))
     p1, d1 = scr.best_pairs(8, kappa)
@@ -86,15 +112,16 @@ def test_screen_best_equals_exhaustive(R, N, M, kappa, fp8):
     assert np.allclose(d1[:n], d2[:n], rtol=1e-5, atol=1e-5 * abs(d2.min()))
 
 
-@pytest.mark.parametrize("fp8", [0, 1])
-def test_screen_with_couplings_and_in_gcd(R, oracle, fp8):
+@pytest.mark.parametrize("form", ["bf16", "fp8", "rank1"])
+def test_screen_with_couplings_and_in_gcd(R, oracle, form):
     """After GCD steps W is nonzero: stored couplings are rescored too, and a
-    screen-driven GCD reaches the oracle's optimum."""
+    screen-driven GCD reaches the oracle's optimum (the rank-one form runs at
+    the first step only, the general bf16 form after it)."""
     N, M = 60, 300
     X = _wl(N, M, 301)
     lam = inputs.default_lambda(N, M, 0.5)
     scr = R.Recon(np.ascontiguousarray(X.T), R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN,
-                  screen_fp8=fp8)
+                  **FORMS[form])
     for _ in range(400):
         delta, obj, m = scr.gcd_step(4, 1.0)
         if delta < 1e-6:
@@ -102,6 +129,7 @@ def test_screen_with_couplings_and_in_gcd(R, oracle, fp8):
     o = oracle.IsingOracle(X, lam)
     oracle.gcd(o, kappa=1.0, eps=1e-9, max_iters=3000)
     assert scr.objective() == pytest.approx(o.objective(), rel=1e-6)
+    assert scr.stats()["screen_rank1"] == (1 if form == "rank1" else 0)
 
 
 def test_screen_gaussian(R, oracle):
@@ -120,26 +148,31 @@ def test_screen_gaussian(R, oracle):
     assert pos <= found
 
 
-def test_fp8_screen_matches_bf16_on_a_larger_lattice(R):
+def test_screen_forms_agree_on_a_larger_lattice(R):
     """Several hundred tiles, M = 200 (K = 448: the fp8 rows end in a half
-    k-block): both operand types give the same best pairs, and the fp8 margin
-    only adds survivors."""
+    k-block; the rank-one rows in 224 of 256 entries): every form gives the same
+    positive-gain best pairs, the fp8 margin only adds survivors, and the
+    rank-one form keeps the fewest."""
     N, M = 6000, 200
     edges = inputs.erdos_renyi(N, 3, inputs.rng(7, inputs.GRAPH))
     w = inputs.rng(7, inputs.COUPLINGS).normal(0, 0.5, len(edges))
     X = inputs.gibbs_ising(N, edges, w, np.zeros(N), M, 100, 7)
     Xs = np.ascontiguousarray(X.T)
     lam = inputs.default_lambda(N, M)
-    out = []
-    for fp8 in (0, 1):
-        c = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
+    out = {}
+    for form in FORMS:
+        c = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, **FORMS[form])
         p, d = c.best_pairs(16, 1.0)
-        out.append((p, d, c.stats()["screen_survivors"]))
+        out[form] = (p, d, c.stats()["screen_survivors"])
         c.close()
-    (p0, d0, s0), (p1, d1, s1) = out
-    assert s1 >= s0
-    assert np.array_equal(d0, d1)
-    assert {tuple(x) for x in p0.tolist()} == {tuple(x) for x in p1.tolist()}
+    s_b, s_f, s_r = out["bf16"][2], out["fp8"][2], out["rank1"][2]
+    assert s_f >= s_b >= s_r
+    p0, d0, _ = out["bf16"]
+    pos0 = {tuple(x) for x, dv in zip(p0.tolist(), d0) if dv < 0}
+    for form in ("fp8", "rank1"):
+        p1, d1, _ = out[form]
+        assert np.array_equal(d0, d1)
+        assert pos0 == {tuple(x) for x, dv in zip(p1.tolist(), d1) if dv < 0}
 
 
 def test_fp8_screen_is_refused_for_the_gaussian_model(R):
@@ -149,15 +182,15 @@ def test_fp8_screen_is_refused_for_the_gaussian_model(R):
     assert e.value.status == R.RECON_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("fp8", [0, 1])
-def test_screen_after_gcd_steps_equals_exhaustive(R, fp8):
+@pytest.mark.parametrize("form", ["bf16", "fp8"])
+def test_screen_after_gcd_steps_equals_exhaustive(R, form):
     """With couplings set (residuals vary per sample, so every rounding error
     differs), the screen's best pairs still equal the exhaustive search's."""
     N, M = 700, 400
     X = _wl(N, M, 77)
     Xs = np.ascontiguousarray(X.T)
     lam = inputs.default_lambda(N, M)
-    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_fp8=fp8)
+    scr = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, **FORMS[form])
     for _ in range(3):
         scr.gcd_step(8, 1.0)
     ij, w, h = scr.get_model()
