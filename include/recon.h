@@ -109,7 +109,11 @@ typedef struct {
                              with the coarser rounding, so the result is still exact, with
                              more survivors to score.
                              RECON_GAUSSIAN: recon_init returns RECON_EUNSUPPORTED */
-    int32_t reserved[3];  /* zero */
+    int32_t screen_no_rank1; /* nonzero: at the empty network (no stored coupling, where every
+                             sample of a node has the same field) the screen still uses the
+                             general form above; by default it computes the spin product
+                             X X^T in E4M3 (exact, K = M) plus a rank-two correction */
+    int32_t reserved[2];  /* zero */
 } recon_options;
 
 typedef struct {
@@ -133,6 +137,9 @@ typedef struct {
     int64_t tuned_threads;    /* block width the autotuner picked for the segmented scorer (0: not yet) */
     int64_t dropped_offers;   /* NNDescent second neighbours past the per-node cap, and offers past
                                  a full offer buffer, skipped for an iteration */
+    int64_t screen_rank1;     /* screen launches in the rank-one form of the empty network */
+    int64_t device_bytes;     /* device memory this context has requested since init (every
+                                 allocation counted; frees are not subtracted) */
 } recon_stats;
 
 /* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,
@@ -348,6 +355,32 @@ recon_status recon_get_stats(recon_ctx *ctx, recon_stats *out);
  * exactly as the saved one would. */
 recon_status recon_save(recon_ctx *ctx, const char *path);
 recon_status recon_load(recon_ctx **out, const char *path, void *stream);
+
+/* ---- device ceilings ------------------------------------------------------
+ * The paper has no counterpart: these are the arithmetic and on-chip bandwidth
+ * ceilings that the kernels' rooflines are stated against, measured on the
+ * device by short fixed-work kernels timed with CUDA events (eight independent
+ * dependency chains per thread, 8 CTAs of 256 threads per SM). */
+typedef struct {
+    int32_t sm_count;        /* streaming multiprocessors */
+    double sm_clock_mhz;     /* the device's reported maximum SM clock */
+    int64_t l2_bytes;        /* L2 cache size */
+    double fp32_tflops;      /* FP32 fused multiply-add, 2 flops each */
+    double fp64_tflops;      /* FP64 fused multiply-add, 2 flops each */
+    double mufu_rcp_gops;    /* rcp.approx.ftz.f32 per second (10^9; with one FP32 add each) */
+    double mufu_ex2_gops;    /* ex2.approx.ftz.f32 per second */
+    double mufu_lg2_gops;    /* lg2.approx.ftz.f32 per second (with one FP32 add each) */
+    double mufu_tanh_gops;   /* tanh.approx.f32 per second */
+    double l2_read_gbs;      /* 16-byte loads from an L2-resident buffer into the SMs, GB/s */
+    double l2_buffer_bytes;  /* size of that buffer (a quarter of L2) */
+} recon_peaks;
+
+/* recon_device_peaks -- measures the ceilings above on CUDA device `device`
+ * (which becomes the calling thread's current device).  Allocates a quarter of
+ * the L2 size of device memory for the call and frees it; changes no device
+ * setting.  Takes a few milliseconds.  RECON_ECUDA if a CUDA call fails;
+ * RECON_EINVAL for out == NULL.  Synchronous. */
+recon_status recon_device_peaks(int32_t device, recon_peaks *out);
 
 /* recon_last_error -- message of the last failed call on ctx (or of the last
  * failed recon_init / recon_load in this thread when ctx is NULL). */

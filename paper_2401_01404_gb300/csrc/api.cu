@@ -756,7 +756,8 @@ extern "C" recon_status recon_get_stats(recon_ctx *c, recon_stats *out) {
     CK(cudaMemcpyAsync(c->cnt_host + CNT_NEWTON, c->cnt + CNT_NEWTON, sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    c->stats.newton_passes = (int64_t)c->cnt_host[CNT_NEWTON];
+    c->stats.newton_passes = (int64_t)c->cnt_host[CNT_NEWTON] + c->newton_extra;
+    c->stats.device_bytes = (int64_t)c->alloc_total;
     for (auto &t : c->timed) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, t.a, t.b));

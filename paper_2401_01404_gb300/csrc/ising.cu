@@ -530,15 +530,20 @@ __global__ void k_objective(IsingView v, double *partials) {
 // bit column) in flight with bulk asynchronous copies into a ring of
 // shared-memory stages, one mbarrier per stage.  Every wait is bounded
 // (about 1 s); a warp that gives up sets ERR_TIMEOUT, lets its copies land
-// (again bounded) and stops.
+// (again bounded) and stops.  The error word is the launch's abort flag: a
+// waiting warp that sees ERR_TIMEOUT there stops waiting, and a block that sees
+// it at its start does no work, so one stall ends the launch in about a second
+// however many blocks it has.
 constexpr int SEG_RING = 2;
 
-__device__ __forceinline__ bool seg_wait(uint64_t *b, uint32_t par) {
+// err: the launch's error word, polled on the slow path (NULL: wait out the bound)
+__device__ __forceinline__ bool seg_wait(uint64_t *b, uint32_t par, const unsigned long long *err) {
     if (mbar_try(b, par)) return true;
     uint64_t t0 = 0;
     for (uint32_t n = 1;; ++n) {
         if (mbar_try(b, par)) return true;
         if ((n & 255u) == 0) {
+            if (err && (*(const volatile unsigned long long *)err & ERR_TIMEOUT)) return false;
             const uint64_t now = gtimer();
             if (t0 == 0)
                 t0 = now;
@@ -559,6 +564,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
     if (sidx >= nseg) return;
     const int count = seg_count[sidx];
     if (count <= 0) return;
+    if (*(const volatile unsigned long long *)(cnt + CNT_ERR) & ERR_TIMEOUT) return;  // the launch gave up
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // layout: row x (Mp floats), its bits (32 words), per warp SEG_RING stages
     // of Mp + 32 words, the stages' mbarriers, then per warp the chunk's ids,
@@ -626,7 +632,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
             const int q = warp + k * nw;
             const int64_t pos = start + q;
             const int s = k % SEG_RING;
-            if (!__all_sync(0xffffffffu, seg_wait(bars + s, (uint32_t)((k / SEG_RING) & 1)))) {
+            if (!__all_sync(0xffffffffu, seg_wait(bars + s, (uint32_t)((k / SEG_RING) & 1), cnt + CNT_ERR))) {
                 ok = false;
                 break;
             }
@@ -661,7 +667,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
         const int base = k / 32 * 32;
         const int nch = min(32, mine - base);
         for (int kk = k; !p.stall && kk < base + nch && kk < k + SEG_RING; ++kk)
-            seg_wait(bars + kk % SEG_RING, (uint32_t)((kk / SEG_RING) & 1));
+            seg_wait(bars + kk % SEG_RING, (uint32_t)((kk / SEG_RING) & 1), nullptr);
     }
     if (lane == 0 && npass) atomicAdd(&cnt[CNT_NEWTON], npass);
 }

@@ -26,6 +26,7 @@ constexpr size_t kWords = 16;            // error / counter words
 constexpr size_t kPairBytes = sizeof(int32_t) * 2 * kMaxPairs;
 constexpr size_t kOutBytes = sizeof(float) * kMaxPairs;
 constexpr size_t kScratchBytes = sizeof(unsigned long long) * kWords + kPairBytes + 2 * kOutBytes;  // 1 MiB + 128 B
+static_assert(kWords >= CNT_N, "the scorer's error and counter words must fit in the array");
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -99,8 +100,16 @@ extern "C" recon_status recon_score_noalloc(recon_ctx *c, const int32_t *pairs, 
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_out, dd, sizeof(float) * P, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && w_out)
             e = cudaMemcpyAsync(w_out, dw, sizeof(float) * P, cudaMemcpyDeviceToHost, c->stream);
+        // the scorer counts its Newton passes in the array's words: carried over to
+        // the context's statistics
+        unsigned long long npass = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&npass, words + CNT_NEWTON, sizeof npass, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e == cudaSuccess) c->stats.pair_evals += P;
+        if (e == cudaSuccess) {
+            c->stats.pair_evals += P;
+            c->newton_extra += (int64_t)npass;
+        }
     }
     if (cur != c->device) cudaSetDevice(cur);
     if (e != cudaSuccess) return cuda_fail(c, e, "recon_score_noalloc");

@@ -31,7 +31,7 @@ class recon_options(C.Structure):
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
                 ("timing", C.c_int32), ("no_graphs", C.c_int32),
                 ("learned_frac", C.c_float), ("distance", C.c_int32), ("screen_fp8", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("screen_no_rank1", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class recon_stats(C.Structure):
@@ -41,7 +41,15 @@ class recon_stats(C.Structure):
                 ("score_launches", C.c_int64), ("score_pairs", C.c_int64), ("score_ms", C.c_double),
                 ("screen_launches", C.c_int64), ("screen_ms", C.c_double), ("screen_flop", C.c_double),
                 ("screen_survivors", C.c_int64), ("seeded_nodes", C.c_int64), ("tuned_threads", C.c_int64),
-                ("dropped_offers", C.c_int64)]
+                ("dropped_offers", C.c_int64), ("screen_rank1", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+
+class recon_peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("sm_clock_mhz", C.c_double), ("l2_bytes", C.c_int64),
+                ("fp32_tflops", C.c_double), ("fp64_tflops", C.c_double), ("mufu_rcp_gops", C.c_double),
+                ("mufu_ex2_gops", C.c_double), ("mufu_lg2_gops", C.c_double), ("mufu_tanh_gops", C.c_double),
+                ("l2_read_gbs", C.c_double), ("l2_buffer_bytes", C.c_double)]
 
 
 class recon_train_opts(C.Structure):
@@ -86,6 +94,7 @@ _EXPORTS = {
     "recon_proposal_weights": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "recon_proposal_embed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "recon_proposal_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "recon_device_peaks": (C.c_int, [C.c_int32, C.c_void_p]),
     "recon_last_error": (C.c_char_p, [C.c_void_p]),
     "recon_destroy": (None, [C.c_void_p]),
 }
@@ -266,7 +275,7 @@ def recon_get_stats(ctx) -> dict:
             "score_pairs": s.score_pairs, "score_ms": s.score_ms, "screen_launches": s.screen_launches,
             "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors,
             "seeded_nodes": s.seeded_nodes, "tuned_threads": s.tuned_threads,
-            "dropped_offers": s.dropped_offers}
+            "dropped_offers": s.dropped_offers, "screen_rank1": s.screen_rank1, "device_bytes": s.device_bytes}
 
 
 def recon_set_list_lengths(ctx, k=None):
@@ -354,6 +363,13 @@ def recon_proposal_grad(ctx, pairs, targets):
     loss = C.c_double()
     _check(lib().recon_proposal_grad(ctx, p.ctypes.data, t.ctypes.data, len(p), g.ctypes.data, C.byref(loss)), ctx)
     return g, loss.value
+
+
+def recon_device_peaks(device: int = 0) -> dict:
+    """The device's measured FP32/FP64 FMA, MUFU and L2-read ceilings (see recon_peaks)."""
+    out = recon_peaks()
+    _check(lib().recon_device_peaks(int(device), C.byref(out)))
+    return {name: getattr(out, name) for name, _ in recon_peaks._fields_}
 
 
 def recon_save(ctx, path: str):

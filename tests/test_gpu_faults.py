@@ -102,3 +102,26 @@ def test_stalled_scorer_times_out_and_the_gpu_stays_usable(R, data):
     fresh = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=ex)
     p1, d1 = fresh.best_pairs(16, 1.0)
     assert np.array_equal(p0, p1) and np.array_equal(d0, d1)
+
+
+def test_stalled_scorer_gives_up_once_for_the_whole_launch(R):
+    """With many more segments than fit on the GPU at once, a stall still ends
+    the launch in about one wait bound: the first warp that gives up raises the
+    launch's error word, the waiting warps see it and later blocks skip their
+    work (rather than each wave of blocks waiting its own second)."""
+    N, M = 3000, 200
+    edges = inputs.erdos_renyi(N, 3, inputs.rng(33, inputs.GRAPH))
+    w = inputs.rng(33, inputs.COUPLINGS).normal(0, 0.5, len(edges))
+    Xs = np.ascontiguousarray(inputs.gibbs_ising(N, edges, w, np.zeros(N), M, 50, 33).T)
+    lam = inputs.default_lambda(N, M)
+    ex = R.RECON_KNN_EXHAUSTIVE  # about 9000 segments of up to 512 pairs
+    c = _with_env("RECON_FAULT_SCORE_STALL", "1", lambda: R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=ex))
+    t0 = time.perf_counter()
+    with pytest.raises(R.ReconError) as e:
+        c.best_pairs(16, 1.0)
+    dt = time.perf_counter() - t0
+    assert e.value.status == R.RECON_ETIMEOUT
+    assert dt < 6.0, dt
+    c.close()
+    fresh = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    fresh.best_pairs(16, 1.0)

@@ -40,9 +40,39 @@ def test_noalloc_matches_recon_score_twice_in_a_row(R):
     for call, seed in enumerate((3, 4)):
         pairs = inputs.random_pairs(wl.N, 5000 + 1000 * call, seed)
         d_ref, w_ref = ctx.score(pairs)
+        st0 = ctx.stats()
         d, w = R.recon_score_noalloc(ctx.ctx, pairs)
+        st1 = ctx.stats()
         assert _close(d, d_ref)
         assert np.allclose(w, w_ref, rtol=1e-5, atol=1e-6)
+        # what the entry point is for: the call requested no device memory, and its
+        # work is counted like recon_score's (pairs and Newton passes)
+        assert st1["device_bytes"] == st0["device_bytes"] > 0
+        assert st1["pair_evals"] - st0["pair_evals"] == len(pairs)
+        assert st1["newton_passes"] >= st0["newton_passes"]
+
+
+def test_noalloc_needs_no_allocation_room(R, monkeypatch):
+    """A context whose allocation cap is what its own set-up took cannot grow
+    recon_score's staging buffers for a larger list; recon_score_noalloc still
+    scores that list."""
+    wl = inputs.config("ising_n100_m200", N=200, M=300, sweeps=50)
+    Xs = wl.samples_major()
+    lam = inputs.default_lambda(wl.N, wl.M)
+    probe = R.Recon(Xs, R.RECON_ISING, lam=lam)
+    base = probe.stats()["device_bytes"]
+    probe.close()
+    monkeypatch.setenv("RECON_FAULT_ALLOC_LIMIT", str(base))
+    ctx = R.Recon(Xs, R.RECON_ISING, lam=lam)
+    monkeypatch.delenv("RECON_FAULT_ALLOC_LIMIT")
+    pairs = inputs.random_pairs(wl.N, 20000, 6)
+    with pytest.raises(R.ReconError) as e:
+        ctx.score(pairs)
+    assert e.value.status == R.RECON_ENOMEM
+    ref = R.Recon(Xs, R.RECON_ISING, lam=lam)
+    for _ in range(2):
+        d, _ = R.recon_score_noalloc(ctx.ctx, pairs)
+        assert _close(d, ref.score(pairs)[0])
 
 
 def test_noalloc_gaussian_and_limits(R):
