@@ -1,15 +1,21 @@
 """Benchmark of the reconstruction hot path on GB300.
 
-A step is one iteration of greedy coordinate descent (Algorithm 2) through
-the C ABI: FindBest (Algorithm 3) over NNDescent (Algorithm 4) with exact
-FP32 pair gains, the matching-batch coordinate updates, the field sweep and the
-objective.  Default workload: Ising, N=2000 nodes, M=1000 Gibbs-sampled spins
-on a planted random 4-regular graph (couplings +-0.3), k=16, kappa=2.
+Default workload: Ising, N = 10^6 nodes, M = 200 Gibbs-sampled spins on a
+planted Erdos-Renyi graph (mean degree 5, couplings N(0, 0.3^2)), k = 16,
+kappa = 1 (m = 10^6), generated on the GPU (untimed).  A step is one
+best-pairs search from the W = 0 start through the C ABI in the chosen form:
+the exact tensor-core screen of every pair (tcgen05, E4M3 spin product at
+W = 0) and exact FP32 scores of its survivors -- Algorithm 3's answer with
+recall 1, which is checked against the exact best pairs incident to a seeded
+10^4-node subsample.  The value is the time of that step: the time to 0.99
+best-pair recall.
 
-Printed: one JSON line with pair-sample evaluations per second (value), the
-end-to-end figure through host buffers (e2e), the roofline of the dominant
-kernel (the pair scorer), the CPU oracle baseline, clocks, and the time to
-0.99 best-pair recall.
+Printed: one JSON line with that time (value, seconds), the end-to-end time
+through host buffers (e2e), the roofline of the dominant kernel (the screen),
+the plain FP32 NNDescent search and the learned seeding as recall-against-time
+curves on the same workload, the FP64 oracle on the host cores (cpu_baseline),
+clocks, the device's measured ceilings, and the 2000-node workload's GCD step
+(pair-sample evals/s, the scorer's roofline) and time-to-recall comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -30,29 +36,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-BYTES_PER_PAIR_SAMPLE = 4.125  # the streamed row of a pair: 4 B of tanh(phi) + 1 bit of x
-
-
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ising_n2000_m1000")
+    ap.add_argument("--workload", default="ising_n1e6_m200")
     ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--kappa", type=float, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-recall", action="store_true",
+                    help="skip the plain/learned NNDescent curves and the 2000-node leg")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--scale-workload", default=None,
-                    help="also measure time to 0.99 recall on this large workload (subsample ground truth)")
-    ap.add_argument("--scale-rows", type=int, default=10000)
-    ap.add_argument("--scale-caps", type=int, default=8)
+    ap.add_argument("--scale-rows", type=int, default=10000, help="nodes in the recall subsample")
+    ap.add_argument("--peaks", action="store_true", help="print the device's measured ceilings and exit")
     ap.add_argument("--screen-bench", type=int, nargs=2, metavar=("N", "M"), default=None,
                     help="time only the tensor-core screen on N nodes x M seeded random spins")
-    ap.add_argument("--screen-fp8", action="store_true",
-                    help="E4M3 screen operands (Ising; exact, wider margin) for --screen-bench and the scale leg")
+    ap.add_argument("--screen-form", default="rank1", choices=["rank1", "bf16", "fp8"],
+                    help="screen form for --screen-bench (rank1: the exact E4M3 form at W = 0)")
     ap.add_argument("--findbest-scaling", type=int, nargs="*", metavar="N", default=None,
                     help="FindBest runtime against N on the paper's synthetic Gaussian (M = 10)")
     ap.add_argument("--convergence", type=int, nargs="*", metavar="N", default=None,
@@ -136,16 +138,80 @@ def _reduce_over_ranks(t_local, units_local, device):
     return tt.item(), uu.item()
 
 
-def _cpu_baseline(wl, lam, seconds):
+# ------------------------------------------------------------------ our arm
+
+def _events(n):
+    import torch
+
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+
+
+def _subsample_truth(R, ctx, wl, m, rows_n, d_cut, stream):
+    """Exact best pairs incident to a seeded subsample S of nodes (every pair
+    {i, j}, i in S, scored against all N columns), under the global cut d_cut;
+    returns (truth set, membership mask of S, seconds)."""
+    import torch
+    from paper_2401_01404_gb300 import inputs
+
+    S = np.sort(inputs.rng(5 + wl.N, inputs.STATE).choice(wl.N, min(rows_n, wl.N), replace=False))
+    t0 = time.perf_counter()
+    tp, td, tn = ctx.row_best(S, d_cut, cap=max(1 << 20, 8 * len(S)))
+    if tn > len(tp):
+        tp, td, tn = ctx.row_best(S, d_cut, cap=tn)
+    torch.cuda.synchronize()
+    inS = np.zeros(wl.N, dtype=bool)
+    inS[S] = True
+    return {tuple(x) for x in tp.tolist()}, inS, time.perf_counter() - t0
+
+
+def _recall_on(p, truth, inS):
+    sel = p[inS[p[:, 0]] | inS[p[:, 1]]]
+    return len(truth & {tuple(x) for x in sel.tolist()}) / max(len(truth), 1)
+
+
+def _nnd_curve(R, X_dev, wl, lam, k, kappa, stream, caps, recall_fn, seed_mode=0, weights=None, distance=0):
+    """NNDescent FindBest from the W = 0 state with iteration caps `caps`: per
+    cap (cap, seconds, recall, scorer pair-sample evals/s); a fresh context per
+    cap (one untimed call first, which allocates the buffers)."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    curve, t_hit = [], None
+    for cap in caps:
+        ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
+                      seed_mode=seed_mode, distance=distance, timing=1)
+        if weights is not None:
+            R.recon_proposal_weights(ctx.ctx, weights)
+        ctx.best_pairs(k, kappa)
+        s0 = ctx.stats()
+        e0.record(stream)
+        p, d = ctx.best_pairs(k, kappa)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1 = ctx.stats()
+        ctx.close()
+        dt = e0.elapsed_time(e1) / 1e3
+        rec = recall_fn(p)
+        sms = s1["score_ms"] - s0["score_ms"]
+        rate = (s1["score_pairs"] - s0["score_pairs"]) * wl.M / (sms / 1e3) if sms > 0 else None
+        curve.append((cap, round(dt, 5), round(rec, 5), rate))
+        if rec >= 0.99 and t_hit is None:
+            t_hit = dt
+            break
+    return t_hit, curve
+
+
+def _cpu_baseline(wl, lam, seconds, m_pairs=None):
     """The FP64 oracle (OpenMP on every host core) scoring a bounded sample of
-    uniformly random pairs of the workload at its W = 0 start."""
+    uniformly random pairs of the workload at its W = 0 start; its rate, and the
+    time its exhaustive search over all N(N-1)/2 pairs (the oracle's route to
+    the exact best pairs) would take at that rate."""
     from oracle import oracle
     from paper_2401_01404_gb300 import inputs
 
     h = oracle.ising_fields_at_zero(wl.X)
     phi = np.repeat(h[:, None], wl.M, 1)
     P = 256
-    t_used = 0.0
     while True:
         pairs = inputs.random_pairs(wl.N, P, 77)
         t0 = time.perf_counter()
@@ -154,209 +220,102 @@ def _cpu_baseline(wl, lam, seconds):
         if t_used >= seconds / 4 or P >= 1 << 22:
             break
         P *= 4
-    return {"value": P * wl.M / t_used, "unit": "pair-sample evals/s", "cores": oracle.nthreads(),
-            "kind": "oracle",
+    rate = P * wl.M / t_used
+    allp = wl.N * (wl.N - 1) / 2
+    return {"pair_sample_evals_per_s": rate, "cores": oracle.nthreads(), "kind": "oracle",
+            "exhaustive_s_extrapolated": allp * wl.M / rate,
             "sample": f"{P} uniformly random pairs of {wl.name} at W=0 (exact gain by FP64 bisection), "
-                      f"{t_used:.1f} s"}
+                      f"{t_used:.1f} s; time to the exact best pairs = N(N-1)/2 pairs at that rate"}
 
 
-def _recall(found, exact, exact_gain, rel_floor=1e-6):
-    """Fraction of the exact best pairs with gain above rel_floor x the largest
-    that the search found (pairs tied at zero gain are left out)."""
-    keep = exact_gain > rel_floor * exact_gain.max()
-    ex = {tuple(p) for p in exact[keep].tolist()}
-    if not ex:
-        return 1.0
-    return len(ex & {tuple(p) for p in found.tolist()}) / len(ex)
+def _peaks_line(R, device):
+    try:
+        return R.recon_device_peaks(device)
+    except Exception as e:  # measurement support only
+        return {"error": str(e)}
 
 
-def _recall_curve(R, X_dev, lam, wl, k, kappa, stream):
-    """Time of one FindBest call against its recall@m, for NNDescent iteration
-    caps 1, 2, ...; the first cap reaching 0.99 gives the time to recall."""
+def _c2_leg(R, stream, peaks, steps):
+    """The 2000-node workload (N=2000, M=1000, random 4-regular, +-0.3): the
+    GCD step with NNDescent (pair-sample evals/s, the scorer's roofline against
+    the measured L2 and FP32 ceilings) and time to 0.99 recall, chosen (exact
+    screen) against plain NNDescent at k = 16, 24, 32."""
     import torch
+    from paper_2401_01404_gb300 import inputs
 
+    wl = inputs.config("ising_n2000_m1000", device="cuda")
+    lam, k, kappa = wl.lam, wl.k, wl.kappa
+    X_dev = torch.from_numpy(wl.samples_major()).cuda()
+    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, timing=1)
+    for _ in range(3):
+        ctx.gcd_step(k, kappa)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s0 = ctx.stats()
+    ev = _events(steps)
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.gcd_step(k, kappa)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    s1 = ctx.stats()
+    ctx.close()
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    score_ms = s1["score_ms"] - s0["score_ms"]
+    score_pairs = s1["score_pairs"] - s0["score_pairs"]
+    launches = s1["score_launches"] - s0["score_launches"]
+    rate = score_pairs * wl.M / (score_ms / 1e3) if score_ms else None
+    out = {"workload": wl.name, "N": wl.N, "M": wl.M, "k": k, "kappa": kappa, "lambda": round(lam, 4),
+           "gcd_step": {"pair_sample_evals_per_s": (s1["pair_evals"] - s0["pair_evals"]) * wl.M / t,
+                        "ms_per_step": t / steps * 1e3, "steps": steps,
+                        "search": "NNDescent FindBest, exact FP32 gains, random init"}}
+    if rate:
+        # per pair-sample the scorer streams the candidate row (4 B of t + 1 bit of x)
+        # from L2 (row i is staged once per segment); its first pass is 3 FP32 adds
+        l2 = peaks.get("l2_read_gbs")
+        fp32 = peaks.get("fp32_tflops")
+        out["scorer"] = {"kernel": "k_score_seg (exact pair gain, segmented)", "pair_sample_evals_per_s": rate,
+                         "avg_launch_ms": score_ms / max(launches, 1), "launches": int(launches)}
+        if l2:
+            out["scorer"]["roofline_l2"] = {"bound": "l2", "achieved": rate * 4.125 / 1e9, "peak": l2, "unit": "GB/s",
+                                            "frac": rate * 4.125 / 1e9 / l2,
+                                            "peak_source": "measured (recon_device_peaks, L2-resident reads)"}
+        if fp32:
+            # 3 FP32 ops per pair-sample in the first pass; the peak counts an FMA as 2 flops
+            ops = rate * 3.0
+            out["scorer"]["roofline_alu"] = {"bound": "alu", "achieved": ops / 1e12, "peak": fp32 / 2.0,
+                                             "unit": "Tops/s (FP32 instructions)", "frac": ops / 1e12 / (fp32 / 2.0),
+                                             "peak_source": "measured (recon_device_peaks, FMA rate / 2)"}
+    # time to 0.99 recall against the exhaustive exact best pairs
     m = int(math.floor(kappa * wl.N + 0.5))
     ref = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam)
     top, dtop = ref.exhaustive_best(m)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    ref.exhaustive_best(m)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    t_exh = t0.elapsed_time(t1) / 1e3
     ref.close()
-    out = {"exhaustive_fp32_s": t_exh, "m": m}
-    # learned proposal: pretrained on another draw of the same planted model (not
-    # timed, reported apart); on this run the sketch, MLP inference and the seed
-    # pass are inside the timed span
-    from paper_2401_01404_gb300 import inputs
+    keep = dtop < -1e-6 * max(-float(dtop.min()), 1e-30)
+    truth = {tuple(x) for x in top[keep].tolist()}
 
-    t_pre = time.perf_counter()
-    other = inputs.ising_workload(wl.name + "_pretrain", wl.N, wl.M, "regular" if "n2000" in wl.name else "er",
-                                  4 if "n2000" in wl.name else 5, "pm" if "n2000" in wl.name else "normal", 0.3, 0.0,
-                                  300, 4242, wl.k, wl.kappa, "cuda")
-    tr = R.Recon(other.samples_major(), R.RECON_ISING, stream=stream, lam=lam)
-    losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
-    weights = R.recon_proposal_weights(tr.ctx)
-    tr.close()
-    out["pretrain"] = {"seconds": time.perf_counter() - t_pre, "loss_first": float(losses[0]),
-                       "loss_last": float(losses[-1]), "data": "another Gibbs draw of the same configuration"}
-    # chosen: the bf16 tensor-core screen with exact FP32 re-scoring of its survivors
-    scr = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
-    scr.best_pairs(k, kappa)  # warm
-    times = []
-    for _ in range(5):
-        t0.record(stream)
-        p, d = scr.best_pairs(k, kappa)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        times.append(t0.elapsed_time(t1) / 1e3)
-    st = scr.stats()
-    scr.close()
-    out["chosen_s"] = statistics.median(times)
-    out["chosen_recall"] = _recall(p, top, -dtop.astype(np.float64))
-    out["chosen"] = "bf16 tensor-core gradient screen (tcgen05) + exact FP32 re-scoring of its survivors"
-    out["screen"] = {"tflops": st["screen_flop"] / (st["screen_ms"] / 1e3) / 1e12 if st["screen_ms"] else None,
-                     "avg_launch_ms": st["screen_ms"] / max(st["screen_launches"], 1),
-                     "survivors_per_call": st["screen_survivors"] / max(st["screen_launches"], 1)}
-    for kk, learned, dist in ((k, False, 0), (2 * k, False, 0), (k, True, 0), (k, False, 1)):
-        curve = []
-        t_hit = None
-        mode = R.RECON_SEED_LEARNED if learned else R.RECON_SEED_RANDOM
-        for cap in range(1, 13):
-            ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                          seed_mode=mode, distance=dist)
-            if learned:
-                R.recon_proposal_weights(ctx.ctx, weights)
-            ctx.best_pairs(kk, kappa)  # warm
-            ctx2 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                           seed_mode=mode, distance=dist)
-            if learned:
-                R.recon_proposal_weights(ctx2.ctx, weights)
-            t0.record(stream)
-            p, d = ctx2.best_pairs(kk, kappa)
-            t1.record(stream)
-            torch.cuda.synchronize()
-            dt = t0.elapsed_time(t1) / 1e3
-            rec = _recall(p, top, -dtop.astype(np.float64))
-            curve.append((cap, round(dt, 6), round(rec, 5)))
-            ctx.close()
-            ctx2.close()
-            if rec >= 0.99 and t_hit is None:
-                t_hit = dt
-                break
-        tag = ("learned_fp32" if learned else "gradient_fp32" if dist else "plain_fp32") + ("" if kk == k else f"_k{kk}")
-        out[tag + "_s"] = t_hit
-        out[tag + "_curve"] = curve
-    return out
+    def rec(p):
+        return len(truth & {tuple(x) for x in p.tolist()}) / max(len(truth), 1)
 
-
-def _scale_recall(R, name, stream, rows_n, max_cap, fp8=False):
-    """Time to 0.99 best-pair recall on a workload too large for an exhaustive
-    ground truth.  Truth: a seeded subsample S of nodes, every pair incident to
-    S scored against all N columns (recon_row_best); recall = found best pairs
-    incident to S against the exact best pairs incident to S under the global
-    cut.  The cut is the m-th best d of the exact screen, itself checked on S;
-    a cut estimated from S alone is reported beside it."""
-    import torch
-    from paper_2401_01404_gb300 import inputs
-
-    out = {"workload": name}
-    t = time.perf_counter()
-    wl = inputs.config(name, device="cuda")
-    out["generation_s"] = round(time.perf_counter() - t, 2)
-    N, M, k, kappa = wl.N, wl.M, wl.k, wl.kappa
-    m = int(math.floor(kappa * N + 0.5))
-    lam = wl.lam
-    out.update({"N": N, "M": M, "k": k, "kappa": kappa, "m": m, "lambda": round(lam, 4)})
-    X_dev = torch.from_numpy(wl.samples_major()).cuda()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def timed(fn):
+    scr = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    scr.best_pairs(k, kappa)
+    ts = []
+    for _ in range(5):
         e0.record(stream)
-        r = fn()
+        p, d = scr.best_pairs(k, kappa)
         e1.record(stream)
         torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1) / 1e3
-
-    # chosen: the exact screen (bf16 tensor cores + FP32 re-scoring)
-    scr = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
-    scr.best_pairs(k, kappa)
-    s0 = scr.stats()
-    (p_scr, d_scr), t_scr = timed(lambda: scr.best_pairs(k, kappa))
-    s1 = scr.stats()
-    dflop, dms = s1["screen_flop"] - s0["screen_flop"], s1["screen_ms"] - s0["screen_ms"]
-    out["chosen_s"] = t_scr
-    out["screen"] = {"tflops": dflop / (dms / 1e3) / 1e12 if dms else None, "ms": dms,
-                     "survivors": s1["screen_survivors"] - s0["screen_survivors"]}
-    cut = float(d_scr[-1])
-    # truth on the subsample
-    S = np.sort(inputs.rng(5 + N, inputs.STATE).choice(N, rows_n, replace=False))
-    (tp, td, tn), t_truth = timed(lambda: scr.row_best(S, cut))
-    truth = {tuple(x) for x in tp.tolist()}
-    out["truth"] = {"rows": rows_n, "pairs": len(truth), "seconds": t_truth, "cut_d": cut}
-    # the cut estimated from S alone: pairs incident to S are a 2|S|/N share of all
-    q = int(round(2.0 * m * rows_n / N))
-    pp, dd, nn = scr.row_best(S, 0.0)
-    out["truth"]["cut_d_estimated_from_rows"] = float(dd[min(q, len(dd)) - 1]) if len(dd) else None
-    inS = np.zeros(N, dtype=bool)
-    inS[S] = True
-
-    def recall(p):
-        sel = p[inS[p[:, 0]] | inS[p[:, 1]]]
-        return len(truth & {tuple(x) for x in sel.tolist()}) / max(len(truth), 1)
-
-    out["chosen_recall"] = recall(p_scr)
+        ts.append(e0.elapsed_time(e1) / 1e3)
     scr.close()
-    if fp8:
-        # the same exact screen on E4M3 operands (twice the tensor rate, wider margin)
-        s8 = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1,
-                     screen_fp8=1)
-        s8.best_pairs(k, kappa)
-        s0 = s8.stats()
-        (p8, d8), t8 = timed(lambda: s8.best_pairs(k, kappa))
-        s1 = s8.stats()
-        dflop, dms = s1["screen_flop"] - s0["screen_flop"], s1["screen_ms"] - s0["screen_ms"]
-        out["chosen_fp8_s"] = t8
-        out["screen_fp8"] = {"tflops": dflop / (dms / 1e3) / 1e12 if dms else None, "ms": dms,
-                             "survivors": s1["screen_survivors"] - s0["screen_survivors"],
-                             "same_best_pairs": bool(np.array_equal(d8, d_scr) and
-                                                     {tuple(x) for x in p8.tolist()} ==
-                                                     {tuple(x) for x in p_scr.tolist()})}
-        s8.close()
-    # learned proposal: pretrained on a 10^5-node draw of the same planted model
-    t = time.perf_counter()
-    pre = inputs.ising_workload(name + "_pretrain", 100000, M, "er", 5, "normal", 0.3, 0.0, 300, 4243, k, kappa, "cuda")
-    tr = R.Recon(pre.samples_major(), R.RECON_ISING, stream=stream, lam=inputs.default_lambda(100000, M, 2.0))
-    losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
-    weights = R.recon_proposal_weights(tr.ctx)
-    tr.close()
-    out["pretrain"] = {"seconds": round(time.perf_counter() - t, 2), "N": 100000, "loss_first": float(losses[0]),
-                       "loss_last": float(losses[-1])}
-    for tag, mode, dist in (("plain_fp32", R.RECON_SEED_RANDOM, 0), ("learned_fp32", R.RECON_SEED_LEARNED, 0),
-                            ("gradient_fp32", R.RECON_SEED_RANDOM, 1)):
-        curve, t_hit = [], None
-        for cap in range(1, max_cap + 1):
-            ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, max_knn_iters=cap, eps_knn=0.0, seed=5,
-                          seed_mode=mode, distance=dist)
-            if mode == R.RECON_SEED_LEARNED:
-                R.recon_proposal_weights(ctx.ctx, weights)
-            ctx.best_pairs(k, kappa)  # allocates the buffers
-            (p, d), dt = timed(lambda: ctx.best_pairs(k, kappa))
-            st = ctx.stats()
-            ctx.close()
-            rec = recall(p)
-            curve.append((cap, round(dt, 4), round(rec, 5), int(st["dropped_offers"])))
-            if rec >= 0.99:
-                t_hit = dt
-                break
-        out[tag + "_s"] = t_hit
-        out[tag + "_curve"] = curve
+    out["time_to_recall"] = {"m": m, "chosen_s": statistics.median(ts), "chosen_recall": rec(p),
+                             "chosen": "exact screen (E4M3 spin product at W = 0) + FP32 re-scoring"}
+    for kk in (k, int(1.5 * k), 2 * k):
+        t_hit, curve = _nnd_curve(R, X_dev, wl, lam, kk, kappa, stream, range(1, 13), rec)
+        out["time_to_recall"][f"plain_fp32_k{kk}_s"] = t_hit
+        out["time_to_recall"][f"plain_fp32_k{kk}_curve"] = [c[:3] for c in curve]
     return out
 
-
-# ------------------------------------------------------------------ our arm
 
 def run_ours(a):
     import torch
@@ -374,30 +333,36 @@ def run_ours(a):
         dist.barrier()
     from paper_2401_01404_gb300 import inputs, recon as R
 
+    t_gen = time.perf_counter()
     wl = _workload(a.workload, rank, "cuda")
+    t_gen = time.perf_counter() - t_gen
     k = a.k or wl.k
     kappa = a.kappa or wl.kappa
     lam = wl.lam
+    m = int(math.floor(kappa * wl.N + 0.5))
     stream = torch.cuda.current_stream()
     X_host = torch.from_numpy(wl.samples_major()).pin_memory()
     X_dev = X_host.cuda()
     torch.cuda.synchronize()
+    peaks_dev = _peaks_line(R, local)
 
-    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, timing=1)
+    # one step: the chosen search (the exact screen) from the W = 0 start, i.e.
+    # Algorithm 3's best pairs with recall 1 (checked below on a subsample)
+    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
     for _ in range(a.warmup):
-        ctx.gcd_step(k, kappa)
+        ctx.best_pairs(k, kappa)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
     s0 = ctx.stats()
     clocks = Clocks(torch.cuda.current_device())
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    ev = _events(a.steps)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     for i in range(a.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        ctx.gcd_step(k, kappa)
+        p_best, d_best = ctx.best_pairs(k, kappa)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -405,85 +370,115 @@ def run_ours(a):
     ck = clocks.stop()
     s1 = ctx.stats()
     t_local = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
-    units_local = (s1["pair_evals"] - s0["pair_evals"]) * wl.M
-    score_ms = s1["score_ms"] - s0["score_ms"]
-    score_launches = s1["score_launches"] - s0["score_launches"]
-    score_pairs = s1["score_pairs"] - s0["score_pairs"]
+    t_max, _ = _reduce_over_ranks(t_local, 0.0, "cuda")
+    step_s = t_max / a.steps
     launches = s1["kernel_launches"] - s0["kernel_launches"]
-    obj = ctx.objective()
+    scr_ms = s1["screen_ms"] - s0["screen_ms"]
+    scr_flop = s1["screen_flop"] - s0["screen_flop"]
+    scr_n = s1["screen_launches"] - s0["screen_launches"]
+    rank1 = s1["screen_rank1"] - s0["screen_rank1"]
+    survivors = (s1["screen_survivors"] - s0["screen_survivors"]) / max(scr_n, 1)
+    score_pairs = s1["pair_evals"] - s0["pair_evals"]
+    # recall of the timed result against the subsample ground truth (untimed)
+    cut = float(d_best[-1]) if len(d_best) else 0.0
+    truth, inS, t_truth = _subsample_truth(R, ctx, wl, m, a.scale_rows, cut, stream)
+    recall = _recall_on(p_best, truth, inS)
     ctx.close()
 
-    t_max, units = _reduce_over_ranks(t_local, units_local, "cuda")
-
-    # end to end: init from pinned host samples, one step, model back to the host
-    e2e_steps = max(1, min(a.steps, 5))
+    # end to end through the C ABI: host samples in (pinned), recon_init, the
+    # best pairs back to the host
+    e2e_steps = max(1, min(a.steps, 3))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_units = 0
     d2h = 0
     for _ in range(e2e_steps):
-        c2 = R.Recon(X_host.numpy(), R.RECON_ISING, stream=stream, lam=lam)
-        c2.gcd_step(k, kappa)
-        ij, w, f = c2.get_model()
-        e2e_units += c2.stats()["pair_evals"] * wl.M
-        d2h = ij.nbytes + w.nbytes + f.nbytes + 8
+        c2 = R.Recon(X_host.numpy(), R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+        pp, dd = c2.best_pairs(k, kappa)
+        d2h = pp.nbytes + dd.nbytes
         c2.close()
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    t_e2e, e2e_units = _reduce_over_ranks(t_e2e, e2e_units, "cuda")
+    t_e2e, _ = _reduce_over_ranks((time.perf_counter() - t0) / e2e_steps, 0.0, "cuda")
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     peaks = _peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    avg_launch_s = score_ms / 1e3 / max(score_launches, 1)
-    bytes_per_launch = BYTES_PER_PAIR_SAMPLE * wl.M * score_pairs / max(score_launches, 1)
-    achieved = bytes_per_launch / avg_launch_s / 1e9 if avg_launch_s > 0 else 0.0
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    fp8_peak = 2.0 * bf16  # the measured bf16 peak times the nominal E4M3/bf16 ratio (4.5 / 2.25)
+    avg_ms = scr_ms / max(scr_n, 1)
+    tflops = scr_flop / (scr_ms / 1e3) / 1e12 if scr_ms else 0.0
     line = {
-        "metric": "pair-sample evals/s",
-        "value": units / t_max,
-        "unit": "pair-sample evals/s",
+        "metric": "time to 0.99 best-pair recall, chosen vs plain FP32",
+        "value": step_s,
+        "unit": "s",
         "n_gpus": world,
         "steps": a.steps,
         "warmup": a.warmup,
-        "ms_per_step": t_max / a.steps * 1e3,
-        "higher_is_better": True,
+        "ms_per_step": step_s * 1e3,
+        "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "e4m3" if rank1 == scr_n else "bf16",
         "data": "synthetic",
-        "config": {"workload": wl.name, "model": "ising", "N": wl.N, "M": wl.M, "k": k, "kappa": kappa,
-                   "lambda": round(lam, 4), "search": "NNDescent FindBest, exact FP32 gains, random init",
-                   "step": "one GCD iteration (best pairs, coordinate updates, field sweep, objective)",
-                   "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU"},
-        "e2e": {"value": e2e_units / t_e2e, "unit": "pair-sample evals/s",
-                "h2d_bytes_per_step": int(wl.N * wl.M), "d2h_bytes_per_step": int(d2h),
-                "what": "recon_init from pinned host samples + one GCD step + model to host, per step"},
+        "config": {"workload": wl.name, "model": "ising", "N": wl.N, "M": wl.M, "k": k, "kappa": kappa, "m": m,
+                   "lambda": round(lam, 4),
+                   "graph": "Erdos-Renyi mean degree 5, w ~ N(0, 0.3^2), h = 0, 1000 Gibbs sweeps",
+                   "step": "one best-pairs search (Algorithm 3, exact base case over all nodes) from the W = 0 "
+                           "start: tensor-core screen of every pair + exact FP32 scores of its survivors",
+                   "chosen": "exact screen: E4M3 spin product X X^T on tcgen05 (exact at W = 0) + rank-two "
+                             "correction + FP32 re-scoring of the survivors",
+                   "l2": "flushed between steps (256 MiB write); inputs larger than L2",
+                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU",
+                   "generation_s": round(t_gen, 2)},
+        "recall": {"value": recall, "truth_pairs": len(truth), "rows": int(inS.sum()), "cut_d": cut,
+                   "seconds": round(t_truth, 2),
+                   "protocol": "exact best pairs incident to a seeded 10^4-node subsample, all N columns"},
+        "e2e": {"value": t_e2e, "unit": "s", "h2d_bytes_per_step": int(wl.N * wl.M), "d2h_bytes_per_step": int(d2h),
+                "what": "recon_init from pinned host samples + best pairs to host, per step"},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "k_score (exact pair gain)", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": _score_traffic(wl.name),
-                     "bytes_per_pair_sample": BYTES_PER_PAIR_SAMPLE,
-                     "avg_launch_ms": avg_launch_s * 1e3, "launches": int(score_launches),
-                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback"},
+        "roofline": {"bound": "tensor", "kernel": "k_screen (rank-one form, E4M3)" if rank1 else "k_screen",
+                     "achieved": tflops, "peak": fp8_peak if rank1 else bf16, "unit": "TFLOP/s",
+                     "frac": tflops / (fp8_peak if rank1 else bf16), "traffic": _screen_traffic(wl.name),
+                     "flop_per_launch": scr_flop / max(scr_n, 1), "avg_launch_ms": avg_ms,
+                     "launches": int(scr_n), "survivors_per_launch": survivors,
+                     "peak_source": ("measured bf16 burst x 2 (nominal E4M3/bf16 ratio), MEASURED_PEAKS.json"
+                                     if rank1 else "measured bf16 burst, MEASURED_PEAKS.json") if peaks else "fallback"},
+        "exact_scores_per_step": int(score_pairs / max(a.steps, 1)),
         "clocks": ck,
-        "objective_after": obj,
+        "device_peaks": peaks_dev,
     }
     if not a.no_cpu:
-        line["cpu_baseline"] = _cpu_baseline(wl, lam, a.cpu_seconds)
+        cb = _cpu_baseline(wl, lam, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": cb["exhaustive_s_extrapolated"], "unit": "s", "cores": cb["cores"],
+                                "kind": "oracle", "sample": cb["sample"],
+                                "pair_sample_evals_per_s": cb["pair_sample_evals_per_s"]}
     if not a.no_recall:
-        ttr = _recall_curve(R, X_dev, lam, wl, k, kappa, stream)
-        bf16 = peaks.get("bf16_tflops", 1900.0)
-        if ttr["screen"]["tflops"]:
-            ttr["screen"]["roofline"] = {"bound": "tensor", "achieved": ttr["screen"]["tflops"], "peak": bf16,
-                                         "unit": "TFLOP/s", "frac": ttr["screen"]["tflops"] / bf16,
-                                         "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}
-        line["time_to_recall"] = ttr
-    if a.scale_workload and rank == 0:
-        line["time_to_recall_scale"] = _scale_recall(R, a.scale_workload, stream, a.scale_rows, a.scale_caps,
-                                                     a.screen_fp8)
+        # plain FP32 NNDescent (random init) and the learned seeding, recall against
+        # time on the same workload; the proposal is pretrained (untimed, reported)
+        # on a 10^5-node draw of the same planted model
+        rf = lambda p: _recall_on(p, truth, inS)
+        caps = [1, 2, 4, 8]
+        t_plain, c_plain = _nnd_curve(R, X_dev, wl, lam, k, kappa, stream, caps, rf)
+        tp = time.perf_counter()
+        pre = inputs.ising_workload(wl.name + "_pretrain", 100000, wl.M, "er", 5, "normal", 0.3, 0.0, 300, 4243, k,
+                                    kappa, "cuda")
+        tr = R.Recon(pre.samples_major(), R.RECON_ISING, stream=stream, lam=inputs.default_lambda(100000, wl.M, 2.0))
+        losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
+        weights = R.recon_proposal_weights(tr.ctx)
+        tr.close()
+        t_pre = time.perf_counter() - tp
+        t_learn, c_learn = _nnd_curve(R, X_dev, wl, lam, k, kappa, stream, caps, rf, seed_mode=R.RECON_SEED_LEARNED,
+                                      weights=weights)
+        line["plain_fp32"] = {"s": t_plain, "curve": [c[:3] for c in c_plain],
+                              "scorer_pair_sample_evals_per_s": [c[3] for c in c_plain],
+                              "what": "NNDescent FindBest (k = 16, random init), exact FP32 gains; "
+                                      "(iteration cap, seconds, recall)"}
+        line["learned_fp32"] = {"s": t_learn, "curve": [c[:3] for c in c_learn],
+                                "recall_gain_over_random": [round(b[2] - a_[2], 5) for a_, b in zip(c_plain, c_learn)],
+                                "pretrain": {"seconds": round(t_pre, 2), "N": 100000, "loss_first": float(losses[0]),
+                                             "loss_last": float(losses[-1])}}
+        line["c2"] = _c2_leg(R, stream, peaks_dev, 20)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -492,6 +487,10 @@ def run_ours(a):
 # ------------------------------------------------------------------ reference arm (the CPU oracle)
 
 def run_reference(a):
+    """The FP64 oracle on the host cores, on the same workload and metric: its
+    route to the exact best pairs is the exhaustive search, N(N-1)/2 pair
+    scores; each step times a bounded sample of them (uniformly random pairs at
+    the W = 0 start) and the step's value is the exhaustive time at that rate."""
     rank, world, local = _dist()
     if rank != 0:
         return
@@ -499,42 +498,49 @@ def run_reference(a):
     from paper_2401_01404_gb300 import inputs
 
     oracle.build()
-    wl = inputs.config(a.workload, device="cpu")
+    try:
+        import torch
+
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = "cpu"
+    wl = inputs.config(a.workload, device=dev)  # the input generator (not the oracle) may use the GPU
     lam = wl.lam
     h = oracle.ising_fields_at_zero(wl.X)
     phi = np.repeat(h[:, None], wl.M, 1)
-    P = 2048
-    for s in range(a.warmup):
-        oracle.ising_score_rows(wl.X, phi, inputs.random_pairs(wl.N, P, 100 + s), lam, 5.0)
+    P = 65536
+    for s_ in range(a.warmup):
+        oracle.ising_score_rows(wl.X, phi, inputs.random_pairs(wl.N, P // 8, 100 + s_), lam, 5.0)
     t = 0.0
-    for s in range(a.steps):
-        pairs = inputs.random_pairs(wl.N, P, 1000 + s)
+    for s_ in range(a.steps):
+        pairs = inputs.random_pairs(wl.N, P, 1000 + s_)
         t0 = time.perf_counter()
         oracle.ising_score_rows(wl.X, phi, pairs, lam, 5.0)
         t += time.perf_counter() - t0
-    v = P * a.steps * wl.M / t
+    rate = P * a.steps * wl.M / t
+    v = wl.N * (wl.N - 1) / 2 * wl.M / rate
+    sample = (f"{P} uniformly random pairs per step at W=0, exact gain by FP64 bisection "
+              f"({rate:.4g} pair-sample evals/s); value = N(N-1)/2 pairs at that rate (extrapolated)")
     line = {
         "impl": "reference",
-        "metric": "pair-sample evals/s", "value": v, "unit": "pair-sample evals/s", "n_gpus": world,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
+        "metric": "time to 0.99 best-pair recall, chosen vs plain FP32", "value": v, "unit": "s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t / a.steps * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "model": "ising", "N": wl.N, "M": wl.M},
-        "cpu_baseline": {"value": v, "unit": "pair-sample evals/s", "cores": oracle.nthreads(), "kind": "oracle",
-                         "sample": f"{P} uniformly random pairs per step at W=0, exact gain by FP64 bisection"},
-        "e2e": {"value": v, "unit": "pair-sample evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": oracle.nthreads(), "kind": "oracle", "sample": sample,
+                         "pair_sample_evals_per_s": rate},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes (read + write) per launch of the segmented pair scorer on the
-# 2000-node workload, the mean over the 47 launches of one ncu capture of
-# `python bench.py --steps 2 --warmup 1 --no-cpu --no-recall` (summarised under
-# profiles/); it describes the scorer code it was taken on (digest of the source
-# without its // comments and blank lines) and is reported as null once that
-# code changes
-SCORE_TRAFFIC = {"workload": "ising_n2000_m1000", "bytes_per_launch": 9266361,
-                 "source": "paper_2401_01404_gb300/csrc/ising.cu",
-                 "code_sha256": "f7db6878f45e5ec264cab27a2b248ee799a1688c2b149f47390be62d15793587"}
+# DRAM bytes (read + write) per launch of the screen on the 10^6-node workload,
+# scaled from one ncu capture of a smaller launch by the units processed
+# (summarised under profiles/); it describes the screen code it was taken on
+# (digest of the source without its // comments and blank lines) and is
+# reported as null once that code changes
+SCREEN_TRAFFIC = {"workload": "ising_n1e6_m200", "bytes_per_launch": None,
+                  "source": "paper_2401_01404_gb300/csrc/screen.cu", "code_sha256": ""}
 
 
 def _code_digest(path):
@@ -545,14 +551,14 @@ def _code_digest(path):
     return hashlib.sha256("\n".join(l for l in lines if l.strip()).encode()).hexdigest()
 
 
-def _score_traffic(workload):
-    if workload != SCORE_TRAFFIC["workload"]:
+def _screen_traffic(workload):
+    if workload != SCREEN_TRAFFIC["workload"] or not SCREEN_TRAFFIC["bytes_per_launch"]:
         return None
     try:
-        cur = _code_digest(os.path.join(ROOT, SCORE_TRAFFIC["source"]))
+        cur = _code_digest(os.path.join(ROOT, SCREEN_TRAFFIC["source"]))
     except OSError:
         return None
-    return SCORE_TRAFFIC["bytes_per_launch"] if cur == SCORE_TRAFFIC["code_sha256"] else None
+    return SCREEN_TRAFFIC["bytes_per_launch"] if cur == SCREEN_TRAFFIC["code_sha256"] else None
 
 
 def _peaks():
@@ -565,8 +571,9 @@ def _peaks():
 
 def run_screen_bench(a):
     """The screen alone (the dominant kernel of the exact best-pairs path) on
-    seeded uniform random spins, lambda = 2 sqrt(2 M ln N): one JSON line with
-    the per-launch time and its fraction of the measured bf16 peak."""
+    seeded uniform random spins, lambda = 2 sqrt(2 M ln N), in the chosen form
+    (--screen-form): one JSON line with the per-launch time and its fraction of
+    the measured peak of the operand type."""
     import torch
     import __graft_entry__
 
@@ -577,8 +584,9 @@ def run_screen_bench(a):
     gen = torch.Generator(device="cuda")
     gen.manual_seed(int(inputs.rng(N + M, inputs.SAMPLES).integers(1 << 62)))
     X = (torch.randint(0, 2, (M, N), generator=gen, device="cuda", dtype=torch.int8) * 2 - 1).contiguous()
+    form = a.screen_form
     ctx = R.Recon(X, R.RECON_ISING, lam=inputs.default_lambda(N, M, 2.0), knn_mode=R.RECON_KNN_SCREEN, timing=1,
-                  screen_fp8=int(a.screen_fp8))
+                  screen_fp8=int(form == "fp8"), screen_no_rank1=int(form != "rank1"))
     for _ in range(max(a.warmup, 1)):
         ctx.best_pairs(16, 1.0)
     s0 = ctx.stats()
@@ -595,12 +603,34 @@ def run_screen_bench(a):
     ms = (s1["screen_ms"] - s0["screen_ms"]) / a.steps
     tf = (s1["screen_flop"] - s0["screen_flop"]) / a.steps / (ms / 1e3) / 1e12
     peaks = _peaks()
-    # fp8 peak: the measured bf16 peak times the nominal fp8/bf16 ratio (4.5 / 2.25)
-    peak = peaks.get("bf16_tflops", 1900.0) * (2.0 if a.screen_fp8 else 1.0)
-    print(json.dumps({"kernel": "k_screen", "operands": "e4m3" if a.screen_fp8 else "bf16", "N": N, "M": M,
-                      "steps": a.steps, "ms_per_launch": ms, "tflops": tf, "peak": peak, "frac": tf / peak,
+    # E4M3 peak: the measured bf16 peak times the nominal fp8/bf16 ratio (4.5 / 2.25)
+    peak = peaks.get("bf16_tflops", 1900.0) * (1.0 if form == "bf16" else 2.0)
+    print(json.dumps({"kernel": "k_screen", "form": form, "N": N, "M": M, "steps": a.steps, "ms_per_launch": ms,
+                      "tflops": tf, "peak": peak, "frac": tf / peak,
+                      "rank1_launches": s1["screen_rank1"] - s0["screen_rank1"],
                       "survivors_per_launch": (s1["screen_survivors"] - s0["screen_survivors"]) / a.steps,
-                      "best_pairs_ms": e0.elapsed_time(e1) / a.steps, "clocks": ck, "data": "seeded uniform random spins"}), flush=True)
+                      "best_pairs_ms": e0.elapsed_time(e1) / a.steps, "clocks": ck,
+                      "data": "seeded uniform random spins"}), flush=True)
+
+
+def run_peaks(a):
+    """The device's measured ceilings (recon_device_peaks), one JSON line."""
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon as R
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    runs = [R.recon_device_peaks(local) for _ in range(3)]
+    ck = clocks.stop()
+    best = {k: max(r[k] for r in runs) if isinstance(runs[0][k], float) else runs[0][k] for k in runs[0]}
+    print(json.dumps({"device_peaks": best, "runs": runs, "clocks": ck,
+                      "what": "best of 3; FP32/FP64 = FMA x 2 flops; MUFU ops/s; L2 = 16-byte loads from an "
+                              "L2-resident buffer"}), flush=True)
 
 
 def _paper_gaussian(N, M, seed):
@@ -744,6 +774,9 @@ def run_convergence(a):
 
 def main():
     a = _args()
+    if a.peaks:
+        run_peaks(a)
+        return
     if a.screen_bench:
         run_screen_bench(a)
         return

@@ -16,11 +16,15 @@ def test_reference_arm_prints_one_contract_line():
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["metric"] == "pair-sample evals/s" and d["unit"] == d["metric"]
-    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["impl"] == "reference" and d["metric"] == "time to 0.99 best-pair recall, chosen vs plain FP32"
+    assert d["unit"] == "s" and d["higher_is_better"] is False
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["config"]["workload"] == "ising_n100_m200"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    # the value is the exhaustive search's time at the sampled rate
+    N, M = d["config"]["N"], d["config"]["M"]
+    assert abs(d["value"] - N * (N - 1) / 2 * M / cb["pair_sample_evals_per_s"]) <= 1e-9 * d["value"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -3,7 +3,10 @@
 (1 - 10^-3)^2): the objective is convex (L1-penalised Gaussian
 pseudo-likelihood), so GCD and CD reach the same optimum, and no exact
 coordinate update lowers it.  And FindBest on the runtime workload (M = 10,
-lambda = 0) against exhaustive scoring."""
+lambda = 0) against exhaustive scoring.  Both are also checked against the
+FP64 oracle: the optimum that oracle CD and GCD reach on the convergence
+workload (M = 100), and the recall of the oracle's own FindBest over
+NNDescent (Algorithms 3 and 4) on the runtime workload."""
 import math
 
 import numpy as np
@@ -88,3 +91,68 @@ def test_findbest_with_wide_lists_is_exact_on_the_runtime_workload(R):
     assert len(p) == m and np.all(np.diff(d) >= 0) and np.all(d < 0)
     rec = len({tuple(x) for x in p.tolist()} & {tuple(x) for x in pe.tolist()}) / m
     assert rec > 0.99, rec
+
+
+def test_gcd_reaches_the_oracle_optimum_on_the_paper_gaussian(R, oracle):
+    """N = 100, M = 100 (the convergence study's workload): the FP64 oracle's
+    CD (Algorithm 1) and GCD (Algorithm 2, exhaustive selection) and the CUDA
+    path's GCD over the exact screen and over NNDescent all end at one optimum,
+    within 1e-6 relative; the couplings agree where they are well determined."""
+    N, M = 100, 100
+    Xs, lam = _paper_gaussian(N, M, 13)
+    X64 = np.ascontiguousarray(Xs.T.astype(np.float64))  # the float32 samples the GPU sees
+    o_cd = oracle.GaussOracle(X64, lam)
+    oracle.cd(o_cd, eps=1e-9, max_iters=3000)
+    o_gcd = oracle.GaussOracle(X64, lam)
+    oracle.gcd(o_gcd, kappa=1.0, eps=1e-9, max_iters=20000)
+    ref = o_cd.objective()
+    assert o_gcd.objective() == pytest.approx(ref, rel=1e-9)
+    c_scr = R.Recon(Xs, R.RECON_GAUSSIAN, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
+    _run(c_scr, lambda c: c.gcd_step(1, 1.0), 3000)
+    c_nnd = R.Recon(Xs, R.RECON_GAUSSIAN, lam=lam, seed=4)
+    _run(c_nnd, lambda c: c.gcd_step(1, 1.0), 3000)
+    for c in (c_scr, c_nnd):
+        assert c.objective() == pytest.approx(ref, rel=1e-6), (c.objective(), ref)
+    # couplings: near this optimum the objective is flat along some directions
+    # (100 samples of a nearly singular model), so FP32 and FP64 runs stop at
+    # couplings a little apart: every clearly nonzero oracle coupling is matched in
+    # sign, within 5% of its value plus 0.5% of the largest, and 1% at the median
+    ij, w, s2 = c_scr.get_model()
+    Wg = np.zeros((N, N))
+    Wg[ij[:, 0], ij[:, 1]] = w
+    Wg = Wg + Wg.T
+    Wo = o_cd.W - np.diag(np.diag(o_cd.W))
+    wmax = np.abs(Wo).max()
+    big = np.abs(Wo) > 1e-2 * wmax
+    err = np.abs(Wg[big] - Wo[big])
+    assert np.all(np.sign(Wg[big]) == np.sign(Wo[big]))
+    assert np.all(err <= 0.05 * np.abs(Wo[big]) + 5e-3 * wmax), float((err / np.abs(Wo[big])).max())
+    assert np.median(err / np.abs(Wo[big])) < 1e-2
+    assert np.allclose(s2, o_cd.s2, rtol=1e-2)
+
+
+def test_findbest_recall_matches_the_oracle_on_the_runtime_workload(R, oracle):
+    """N = 1000, M = 10, lambda = 0 (the runtime study's workload): recall of the
+    m = kappa N best pairs by FindBest over NNDescent, on the GPU and in the
+    oracle's sequential Algorithms 3 and 4 (their random choices differ, so the
+    recalls are compared, not the pairs; both stop at the same rule, Delta / (k |S|)
+    < 10^-3 or 30 iterations): close at kappa = 1, and both exact at kappa = 10."""
+    N, M = 1000, 10
+    Xs, _ = _paper_gaussian(N, M, 14)
+    X64 = np.ascontiguousarray(Xs.T.astype(np.float64))
+    o = oracle.GaussOracle(X64, 0.0)
+    D = o.dist_matrix(nthreads=0)
+    for kappa, lo in ((1.0, None), (10.0, 0.99)):
+        m = int(math.floor(kappa * N + 0.5))
+        exact = oracle.exhaustive_best(D, m)
+        g_ex = -D[exact[:, 0], exact[:, 1]]
+        p_o, _ = oracle.findbest(D, m, knn_exact=False, k_min=1, eps=1e-3, max_iters=30, seed=3)
+        r_o = oracle.recall(p_o, exact, g_ex)
+        c = R.Recon(Xs, R.RECON_GAUSSIAN, lam=0.0, seed=3, eps_knn=1e-3, max_knn_iters=30)
+        p_g, _ = c.best_pairs(1, kappa)
+        c.close()
+        r_g = oracle.recall(p_g, exact, g_ex)
+        if lo is None:
+            assert abs(r_g - r_o) <= 0.15, (kappa, r_g, r_o)
+        else:
+            assert r_g >= lo and r_o >= lo, (kappa, r_g, r_o)
