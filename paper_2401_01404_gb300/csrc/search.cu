@@ -7,11 +7,19 @@
 //   1. U = the undirected version of G: each node's k out-neighbours plus at
 //      most k of its in-neighbours, sampled afresh every iteration (the cap on
 //      second neighbours of Sec. III);
-//   2. candidates of x: second neighbours v in U(U(x)) with v > x, deduplicated
-//      in shared memory, minus x's own list; a candidate is generated only if
-//      one of the two U-edges that lead to it is new since the last iteration,
-//      so a pair reached along the same path is scored once (the role of the
-//      score cache of App. B);
+//   2. candidates of x: second neighbours v in U(U(x)), v != x, deduplicated
+//      in shared memory, minus x's own list.  A path x - j - v whose reverse
+//      v - j - x exists too (x in U(j) and j in U(v)) is taken from its smaller
+//      end only, so that the pair is scored once; a path without its reverse
+//      (U is not symmetric when in-neighbours are sampled) is taken from x
+//      whatever the order, as Algorithm 4 has each node search all its own
+//      second neighbours.  A path is taken only if one of its two edges is new
+//      since the last iteration: an undirected edge {x, y} is new when a list
+//      entry between x and y is new, or when one of them took the other's entry
+//      as an in-edge for the first time since the previous iteration (so no
+//      path through a once-unsampled in-edge is skipped for good).  This plays
+//      the role of the score cache of App. B: a pair reached along the same
+//      path is scored once;
 //   3. each canonical candidate pair is scored once (the exact gain) and
 //      offered to both endpoints if it beats their worst entry;
 //   4. each list becomes the best k of (old list u offers), old entries winning
@@ -129,11 +137,14 @@ __global__ void k_in_fill(int64_t nk, const int32_t *ids, const int64_t *inoff, 
 }
 
 // U(x) = out(x) u (at most in_cap in-neighbours, smallest random priority)
+// an in-edge (slot e of a list) counts as new when its entry is new or when it
+// was not in U in the previous iteration (in_last[e] holds the iteration that
+// last took it, in_fresh[e] the iteration that took it without the one before)
 __global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Ucap, const unsigned long long *seed0,
                           const int *iter,
                           const int32_t *ids,
                           const uint8_t *isnew, const int64_t *inoff, const int32_t *indeg, const int32_t *in_e,
-                          int32_t *U, uint8_t *Uf, int32_t *Udeg) {
+                          int32_t *in_last, int32_t *in_fresh, int32_t *U, uint8_t *Uf, int32_t *Udeg) {
     extern __shared__ int32_t sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -180,7 +191,12 @@ __global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Uca
             e_sel = best_e;
         }
         const int y = e_sel / K;
-        const int fl = isnew[e_sel];
+        const int it = *iter, prev = in_last[e_sel];
+        const int fl = isnew[e_sel] || prev != it - 1;
+        if (lane == 0) {
+            in_last[e_sel] = it;
+            if (prev != it - 1) in_fresh[e_sel] = it;
+        }
         int found = -1;
         for (int r = lane; r < k; r += 32)
             if (sid[r] == y) found = r;
@@ -203,6 +219,34 @@ __global__ void k_build_U(int n, int K, const int32_t *klen, int in_cap, int Uca
     if (lane == 0) Udeg[x] = d;
 }
 
+// per U entry (x, a) -> y: Usym = whether x is in U(y), and Uf becomes the
+// undirected edge's flag: new if any list entry between x and y (x -> y at
+// position a < k_x, y -> x wherever x sits in y's list) is new or was taken as
+// an in-edge for the first time this iteration
+__global__ void k_U_sym(int n, int K, const int32_t *klen, int Ucap, const int *iter, const int32_t *ids,
+                        const uint8_t *isnew, const int32_t *in_fresh, const int32_t *U, uint8_t *Uf,
+                        const int32_t *Udeg, uint8_t *Usym) {
+    const int lane = threadIdx.x & 31;
+    const int x = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (x >= n) return;
+    const int it = *iter, degx = Udeg[x], kx = klen[x];
+    for (int a = lane; a < degx; a += 32) {
+        const int y = U[(int64_t)x * Ucap + a];
+        bool sym = false;
+        const int degy = Udeg[y];
+        for (int b = 0; b < degy && !sym; ++b) sym = U[(int64_t)y * Ucap + b] == x;
+        uint8_t f = Uf[(int64_t)x * Ucap + a];
+        if (a < kx) f |= in_fresh[(int64_t)x * K + a] == it;
+        const int ky = klen[y];
+        for (int r = 0; r < ky; ++r) {
+            const int64_t e = (int64_t)y * K + r;
+            if (ids[e] == x) f |= isnew[e] | (uint8_t)(in_fresh[e] == it);
+        }
+        Uf[(int64_t)x * Ucap + a] = f;
+        Usym[(int64_t)x * Ucap + a] = sym;
+    }
+}
+
 __device__ __forceinline__ int sh_insert(int32_t *h, int hmask, int32_t v) {
     uint32_t s = ((uint32_t)v * 2654435761u) & (uint32_t)hmask;
     for (int probe = 0; probe <= hmask; ++probe) {
@@ -214,9 +258,11 @@ __device__ __forceinline__ int sh_insert(int32_t *h, int hmask, int32_t v) {
     return -1;
 }
 
-// candidates of x: v in U(U(x)), v > x, not in x's list, reached by a new edge
+// candidates of x: v in U(U(x)), v != x, not in x's list, reached by a new edge
+// (paths with a reverse path from the smaller end only)
 __global__ void k_gen(int n, int K, const int32_t *klen, int Ucap, const int32_t *U, const uint8_t *Uf,
-                      const int32_t *Udeg, const int32_t *ids, int hsize, int lcap, int32_t *cand, int64_t cap,
+                      const uint8_t *Usym, const int32_t *Udeg, const int32_t *ids, int hsize, int lcap,
+                      int32_t *cand, int64_t cap,
                       unsigned long long *counter, unsigned long long *cnt, int32_t *seg_node, int64_t *seg_start,
                       int32_t *seg_count) {
     extern __shared__ int32_t sm[];
@@ -236,11 +282,14 @@ __global__ void k_gen(int n, int K, const int32_t *klen, int Ucap, const int32_t
     for (int a = 0; a < degx; ++a) {
         const int j = U[(int64_t)x * Ucap + a];
         const int fxj = Uf[(int64_t)x * Ucap + a];
+        const int sxj = Usym[(int64_t)x * Ucap + a];
         const int degj = Udeg[j];
         for (int b = lane; b < degj; b += 32) {
             const int v = U[(int64_t)j * Ucap + b];
             const int fjv = Uf[(int64_t)j * Ucap + b];
-            if (v > x && (fxj | fjv)) {
+            // from the smaller end when the reverse path v - j - x exists, else from x
+            const bool mine = v > x || !(sxj && Usym[(int64_t)j * Ucap + b]);
+            if (v != x && (fxj | fjv) && mine) {
                 // past the per-node cap the remaining second neighbours are
                 // skipped this iteration (the paper's cap on the second-neighbour
                 // loop); they stay reachable in later iterations
@@ -1014,6 +1063,11 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     GROW(S.U, sizeof(int32_t) * (size_t)n * Ucap);
     GROW(S.Uf, sizeof(uint8_t) * (size_t)n * Ucap);
     GROW(S.Udeg, sizeof(int32_t) * n);
+    GROW(S.in_last, sizeof(int32_t) * nk);
+    GROW(S.in_fresh, sizeof(int32_t) * nk);
+    GROW(S.Usym, sizeof(uint8_t) * (size_t)n * Ucap);
+    CKS(launch_fill_i32((int32_t *)S.in_last.p, -1, nk, c->stream));
+    CKS(launch_fill_i32((int32_t *)S.in_fresh.p, -1, nk, c->stream));
     GROW(S.scan_in, sizeof(int64_t) * (n + 1));
     GROW(S.scan_tmp, sizeof(int64_t) * scan_tmp_elems(n + 1));
     const int raw = Ucap * Ucap;
@@ -1025,8 +1079,8 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     const size_t smem_gen = per_warp * warps_per_block;
     if (smem_gen > 48 * 1024)
         CKS(cudaFuncSetAttribute(k_gen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_gen));
-    // node x has at most min(raw, n-1-x) candidates
-    const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * lcap, (int64_t)n * (n - 1) / 2), 1);
+    // node x has at most min(raw, n-1) candidates
+    const int64_t cand_cap = std::max<int64_t>(std::min<int64_t>((int64_t)n * lcap, (int64_t)n * (n - 1)), 1);
     GROW(S.cand, sizeof(int32_t) * 2 * cand_cap);
     GROW(S.cand_d, sizeof(float) * cand_cap);
     GROW(S.seg_node, sizeof(int32_t) * n);
@@ -1098,13 +1152,20 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
             k_build_U<<<nblk((int64_t)n * 32, 32 * wpb), 32 * wpb, smem, gs>>>(
                 n, k, klen, in_cap, Ucap, (const unsigned long long *)S.seed.p, (int *)S.iter.p, (int32_t *)S.knn_id.p,
                 (uint8_t *)S.knn_new.p,
-                (int64_t *)S.inoff.p, (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
+                (int64_t *)S.inoff.p, (int32_t *)S.indeg.p, (int32_t *)S.in_e.p, (int32_t *)S.in_last.p,
+                (int32_t *)S.in_fresh.p, (int32_t *)S.U.p, (uint8_t *)S.Uf.p,
                 (int32_t *)S.Udeg.p);
             note_launch();
         }
+        k_U_sym<<<nblk((int64_t)n * 32, 256), 256, 0, gs>>>(n, k, klen, Ucap, (int *)S.iter.p, (int32_t *)S.knn_id.p,
+                                                          (uint8_t *)S.knn_new.p, (int32_t *)S.in_fresh.p,
+                                                          (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p,
+                                                          (uint8_t *)S.Usym.p);
+        note_launch();
         if ((e = cudaMemsetAsync(c->cnt + CNT_SCRATCH0, 0, sizeof(unsigned long long) * 4, gs))) return e;
         k_gen<<<nblk((int64_t)n * 32, 32 * warps_per_block), 32 * warps_per_block, smem_gen, gs>>>(
-            n, k, klen, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (int32_t *)S.Udeg.p, (int32_t *)S.knn_id.p, hsize,
+            n, k, klen, Ucap, (int32_t *)S.U.p, (uint8_t *)S.Uf.p, (uint8_t *)S.Usym.p, (int32_t *)S.Udeg.p,
+            (int32_t *)S.knn_id.p, hsize,
             lcap, (int32_t *)S.cand.p, cand_cap, counter(c, CNT_SCRATCH0), c->cnt, (int32_t *)S.seg_node.p,
             (int64_t *)S.seg_start.p, (int32_t *)S.seg_count.p);
         note_launch();
@@ -1159,7 +1220,8 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
                                 threads, stride_grid, c->model};
         put(ints, sizeof ints);
         const void *ptrs[] = {klen, gid, ea, eb, gs, c->cnt, c->cnt_host, S.knn_id.p, S.knn_d.p, S.knn_new.p,
-                              S.indeg.p, S.inoff.p, S.cursor.p, S.in_e.p, S.U.p, S.Uf.p, S.Udeg.p, S.scan_in.p,
+                              S.indeg.p, S.inoff.p, S.cursor.p, S.in_e.p, S.in_last.p, S.in_fresh.p, S.Usym.p,
+                              S.U.p, S.Uf.p, S.Udeg.p, S.scan_in.p,
                               S.scan_tmp.p, S.cand.p, S.cand_d.p, S.seg_node.p, S.seg_start.p, S.seg_count.p,
                               S.off_t.p, S.off_v.p, S.off_d.p, S.off_sv.p, S.off_sd.p, S.iter.p, S.seed.p};
         put(ptrs, sizeof ptrs);

@@ -8,7 +8,8 @@
 struct SearchBufs {
     DBuf knn_id, knn_d, knn_new;                  // lists of the current level
     DBuf indeg, inoff, cursor, in_e;              // reverse edges
-    DBuf U, Uf, Udeg;                             // undirected view
+    DBuf in_last, in_fresh;                       // per list slot: iterations that took it into U
+    DBuf U, Uf, Udeg, Usym;                       // undirected view
     DBuf scan_in, scan_tmp, scan_tmp2;            // scans
     DBuf cand, cand_d;                            // candidate pairs and scores
     DBuf seg_node, seg_start, seg_count, seg_vbase;  // candidates grouped by first node
@@ -37,7 +38,7 @@ struct SearchBufs {
     bool g0_moved = false;
 
     std::vector<DBuf *> all() {
-        return {&knn_id, &knn_d, &knn_new, &indeg, &inoff, &cursor, &in_e, &U, &Uf, &Udeg,
+        return {&knn_id, &knn_d, &knn_new, &indeg, &inoff, &cursor, &in_e, &in_last, &in_fresh, &U, &Uf, &Udeg, &Usym,
                 &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &seg_node, &seg_start, &seg_count, &seg_vbase, &off_t, &off_v, &off_d, &off_sv,
                 &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
                 &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
