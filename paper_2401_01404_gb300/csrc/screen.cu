@@ -318,12 +318,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     // (straight-line issue: a data-dependent branch between the MMAs of a
                     // k-block cost the bf16 path about a tenth of its throughput)
                     if constexpr (F8) {
-                        if (kb + 1 < a.nk || a.last_mma == 4) {
+                        // the k-block's MMA count is chosen once, before the first MMA:
+                        // each count issues its MMAs in straight line
+                        const int nm = kb + 1 < a.nk ? 4 : a.last_mma;
+                        if (nm == 4) {
 #pragma unroll
                             for (int k = 0; k < 4; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        } else if (nm == 3) {
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        } else if (nm == 2) {
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                         } else {
-                            for (int k = 0; k < a.last_mma; ++k)
-                                mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                            mma_fp8(d, da, db, idesc, kb != 0);
                         }
                     } else {
 #pragma unroll
