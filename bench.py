@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale-rows", type=int, default=10000, help="nodes in the recall subsample")
     ap.add_argument("--peaks", action="store_true", help="print the device's measured ceilings and exit")
+    ap.add_argument("--gcd-step", action="store_true",
+                    help="time only the GCD step with NNDescent on --workload (default the 2000-node one)")
     ap.add_argument("--screen-bench", type=int, nargs=2, metavar=("N", "M"), default=None,
                     help="time only the tensor-core screen on N nodes x M seeded random spins")
     ap.add_argument("--screen-form", default="rank1", choices=["rank1", "bf16", "fp8"],
@@ -108,20 +110,11 @@ class Clocks:
 
 # ------------------------------------------------------------------ workload
 
-def _workload(name, rank, device, N=None, M=None, sweeps=None):
-    """The named workload; rank r > 0 gets an independent replica (a new draw
-    of the same planted model, same sizes and penalty).  N, M, sweeps shrink it
-    (tests)."""
+def _workload(name, device, N=None, M=None, sweeps=None):
+    """The named workload (N, M, sweeps shrink it for tests)."""
     from paper_2401_01404_gb300 import inputs
 
-    wl = inputs.config(name, device=device, N=N, M=M, sweeps=sweeps)
-    if rank:
-        lam = wl.lam
-        wl = inputs.ising_workload(name, wl.N, wl.M, "regular" if "n2000" in name else "er",
-                                   4 if "n2000" in name else 5, "pm" if "n2000" in name else "normal",
-                                   0.3, 0.0, sweeps or 1000, 2000 + 7919 * rank, wl.k, wl.kappa, device)
-        wl.lam = lam
-    return wl
+    return inputs.config(name, device=device, N=N, M=M, sweeps=sweeps)
 
 
 def _reduce_over_ranks(t_local, units_local, device):
@@ -235,7 +228,7 @@ def _peaks_line(R, device):
         return {"error": str(e)}
 
 
-def _c2_leg(R, stream, peaks, steps):
+def _c2_leg(R, stream, peaks, steps, workload="ising_n2000_m1000", recall=True):
     """The 2000-node workload (N=2000, M=1000, random 4-regular, +-0.3): the
     GCD step with NNDescent (pair-sample evals/s, the scorer's roofline against
     the measured L2 and FP32 ceilings) and time to 0.99 recall, chosen (exact
@@ -243,7 +236,7 @@ def _c2_leg(R, stream, peaks, steps):
     import torch
     from paper_2401_01404_gb300 import inputs
 
-    wl = inputs.config("ising_n2000_m1000", device="cuda")
+    wl = inputs.config(workload, device="cuda")
     lam, k, kappa = wl.lam, wl.k, wl.kappa
     X_dev = torch.from_numpy(wl.samples_major()).cuda()
     ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, timing=1)
@@ -286,6 +279,8 @@ def _c2_leg(R, stream, peaks, steps):
             out["scorer"]["roofline_alu"] = {"bound": "alu", "achieved": ops / 1e12, "peak": fp32 / 2.0,
                                              "unit": "Tops/s (FP32 instructions)", "frac": ops / 1e12 / (fp32 / 2.0),
                                              "peak_source": "measured (recon_device_peaks, FMA rate / 2)"}
+    if not recall:
+        return out
     # time to 0.99 recall against the exhaustive exact best pairs
     m = int(math.floor(kappa * wl.N + 0.5))
     ref = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam)
@@ -331,10 +326,12 @@ def run_ours(a):
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
-    from paper_2401_01404_gb300 import inputs, recon as R
+    from paper_2401_01404_gb300 import inputs, recon as R, shards
 
+    # several GPUs split one search: every rank holds the same data and covers its
+    # shard of the screen's units; the shards' best pairs are gathered and merged
     t_gen = time.perf_counter()
-    wl = _workload(a.workload, rank, "cuda")
+    wl = _workload(a.workload, "cuda")
     t_gen = time.perf_counter() - t_gen
     k = a.k or wl.k
     kappa = a.kappa or wl.kappa
@@ -348,9 +345,16 @@ def run_ours(a):
 
     # one step: the chosen search (the exact screen) from the W = 0 start, i.e.
     # Algorithm 3's best pairs with recall 1 (checked below on a subsample)
-    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1)
+    sopt = shards.shard_options(rank, world)
+    ctx = R.Recon(X_dev, R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, timing=1, **sopt)
+
+    def search(c):
+        if world > 1:
+            return shards.best_pairs_sharded(c.ctx, k, kappa, wl.N)
+        return c.best_pairs(k, kappa)
+
     for _ in range(a.warmup):
-        ctx.best_pairs(k, kappa)
+        search(ctx)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # larger than the 129 MB L2
     s0 = ctx.stats()
     clocks = Clocks(torch.cuda.current_device())
@@ -362,7 +366,7 @@ def run_ours(a):
     for i in range(a.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        p_best, d_best = ctx.best_pairs(k, kappa)
+        p_best, d_best = search(ctx)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -392,8 +396,8 @@ def run_ours(a):
     t0 = time.perf_counter()
     d2h = 0
     for _ in range(e2e_steps):
-        c2 = R.Recon(X_host.numpy(), R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
-        pp, dd = c2.best_pairs(k, kappa)
+        c2 = R.Recon(X_host.numpy(), R.RECON_ISING, stream=stream, lam=lam, knn_mode=R.RECON_KNN_SCREEN, **sopt)
+        pp, dd = search(c2)
         d2h = pp.nbytes + dd.nbytes
         c2.close()
     torch.cuda.synchronize()
@@ -417,7 +421,7 @@ def run_ours(a):
         "warmup": a.warmup,
         "ms_per_step": step_s * 1e3,
         "higher_is_better": False,
-        "scaling": "weak",
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None,
         "dtype": "e4m3" if rank1 == scr_n else "bf16",
         "data": "synthetic",
@@ -429,7 +433,8 @@ def run_ours(a):
                    "chosen": "exact screen: E4M3 spin product X X^T on tcgen05 (exact at W = 0) + rank-two "
                              "correction + FP32 re-scoring of the survivors",
                    "l2": "flushed between steps (256 MiB write); inputs larger than L2",
-                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU",
+                   "parallelism": (f"one search split over {world} GPUs (screen shards, one gather of the "
+                                   f"shards' best pairs, merge on the GPU)") if world > 1 else "single GPU",
                    "generation_s": round(t_gen, 2)},
         "recall": {"value": recall, "truth_pairs": len(truth), "rows": int(inS.sum()), "cut_d": cut,
                    "seconds": round(t_truth, 2),
@@ -479,6 +484,17 @@ def run_ours(a):
                                 "pretrain": {"seconds": round(t_pre, 2), "N": 100000, "loss_first": float(losses[0]),
                                              "loss_last": float(losses[-1])}}
         line["c2"] = _c2_leg(R, stream, peaks_dev, 20)
+        # the paper's synthetic Gaussian workloads at small sizes: FindBest runtime
+        # against N (its runtime figure's workload) and GCD against CD (its
+        # convergence figure's workload); bench.py --findbest-scaling / --convergence
+        # run the larger sizes
+        fs = _findbest_scaling(R, [1000, 10000, 100000], stream)
+        line["paper_runtime_workload"] = {"fit": fs["fit"], "rows": [
+            {"N": r["N"], **{kk: {q: r[kk][q] for q in ("findbest_s", "exhaustive_s", "recall_vs_exhaustive")
+                                  if q in r[kk]} for kk in r if kk.startswith("kappa")}} for r in fs["findbest_scaling"]]}
+        cv = _convergence(R, [100, 1000], stream)
+        line["paper_convergence_workload"] = [{"N": r["N"], "time_to_optimum_s": r["time_to_optimum"],
+                                               "iterations": r["iterations"]} for r in cv["convergence"]]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -613,6 +629,22 @@ def run_screen_bench(a):
                       "data": "seeded uniform random spins"}), flush=True)
 
 
+def run_gcd_step(a):
+    """The GCD step alone (NNDescent FindBest with exact FP32 gains, the
+    coordinate updates, the field sweep, the objective) on --workload (default
+    the 2000-node one), with the scorer's rooflines: one JSON line."""
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon as R
+
+    wl = a.workload if a.workload != "ising_n1e6_m200" else "ising_n2000_m1000"
+    out = _c2_leg(R, torch.cuda.current_stream(), _peaks_line(R, torch.cuda.current_device()), a.steps, wl,
+                  recall=False)
+    print(json.dumps(out), flush=True)
+
+
 def run_peaks(a):
     """The device's measured ceilings (recon_device_peaks), one JSON line."""
     import torch
@@ -648,22 +680,17 @@ def _paper_gaussian(N, M, seed):
     return np.ascontiguousarray(X.T.astype(np.float32)), lam, len(e)
 
 
-def run_findbest_scaling(a):
+def _findbest_scaling(R, sizes, stream, exhaustive_max=50000):
     """FindBest (Algorithm 3 over NNDescent) on the paper's runtime workload
-    (M = 10) for growing N and several kappa (k = ceil(4m/N) = 4 kappa), next to
-    exhaustive scoring of all pairs (up to 5 10^4 nodes), with NNDescent's recall
-    of the exhaustive best pairs.  The penalty is 0: with M = 10 a penalty at
-    the sparsity level exceeds every attainable |a_ij| <= 2 M sigma_i sigma_j, and
-    at lambda = 0 every pair has the gain a^2 / (2 b) > 0 (the exact screen keeps
-    every pair there, so it is not the baseline). One JSON line."""
+    (M = 10) for growing N and kappa = 1, 10 (k = ceil(4m/N) = 4 kappa), next to
+    exhaustive scoring of all pairs (up to `exhaustive_max` nodes), with
+    NNDescent's recall of the exhaustive best pairs.  The penalty is 0: with
+    M = 10 a penalty at the sparsity level exceeds every attainable
+    |a_ij| <= 2 M sigma_i sigma_j, and at lambda = 0 every pair has the gain
+    a^2 / (2 b) > 0 (the exact screen keeps every pair there, so it is not the
+    baseline)."""
     import torch
-    import __graft_entry__
 
-    __graft_entry__.build()
-    from paper_2401_01404_gb300 import recon as R
-
-    sizes = a.findbest_scaling or [1000, 10000, 100000, 1000000]
-    stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
@@ -687,13 +714,12 @@ def run_findbest_scaling(a):
             (p, d), ent["findbest_s"] = timed(lambda: c.best_pairs(1, kappa))
             st = c.stats()
             ent.update({"levels": st["levels"], "knn_iters": st["knn_iters"], "pair_evals": st["pair_evals"]})
-            if N <= 50000:  # the exhaustive k-NN holds a dense N x N score matrix
+            if N <= exhaustive_max:  # the exhaustive k-NN holds a dense N x N score matrix
                 (pe, de), ent["exhaustive_s"] = timed(lambda: c.exhaustive_best(m))
                 ent["recall_vs_exhaustive"] = len({tuple(x) for x in pe.tolist()} & {tuple(x) for x in p.tolist()}) / m
             c.close()
             row[f"kappa{int(kappa)}"] = ent
         rows.append(row)
-        print(json.dumps(row), flush=True)
     fit = {}
     for kappa in (1, 10):
         sel = [r for r in rows if f"kappa{kappa}" in r]
@@ -702,24 +728,29 @@ def run_findbest_scaling(a):
         if len(n) >= 2:
             fit[f"kappa{kappa}_loglog_slope"] = float(np.polyfit(np.log(n), np.log(t), 1)[0])
             fit[f"kappa{kappa}_t_over_NlogN2"] = (t / (n * np.log(n) ** 2)).tolist()
-    print(json.dumps({"findbest_scaling": rows, "fit": fit, "M": 10,
-                      "data": "paper's synthetic Gaussian (ER deg 5, W_ij ~ N(-1e3, 10^2))"}), flush=True)
+    return {"findbest_scaling": rows, "fit": fit, "M": 10,
+            "data": "paper's synthetic Gaussian (ER deg 5, W_ij ~ N(-1e3, 10^2))"}
 
 
-def run_convergence(a):
-    """Algorithm 2 (GCD, FindBest by the exact screen or by NNDescent) against
-    coordinate descent on all pairs, objective against wall time, on the
-    paper's convergence workload (M = 100). CD iteration: every pair scored
-    exhaustively, the pairs with a positive gain updated in order of gain, then
-    the diagonal; GCD iteration: recon_gcd_step(k, kappa). One JSON line."""
+def run_findbest_scaling(a):
     import torch
     import __graft_entry__
 
     __graft_entry__.build()
     from paper_2401_01404_gb300 import recon as R
 
-    sizes = a.convergence or [100, 1000, 10000]
-    stream = torch.cuda.current_stream()
+    print(json.dumps(_findbest_scaling(R, a.findbest_scaling or [1000, 10000, 100000, 1000000],
+                                       torch.cuda.current_stream())), flush=True)
+
+
+def _convergence(R, sizes, stream, cd_iters=60, gcd_iters=400):
+    """Algorithm 2 (GCD, FindBest by the exact screen or by NNDescent) against
+    coordinate descent on all pairs, objective against wall time, on the
+    paper's convergence workload (M = 100). CD iteration: every pair scored
+    exhaustively, the pairs with a positive gain updated in order of gain, then
+    the diagonal; GCD iteration: recon_gcd_step(k, kappa)."""
+    import torch
+
     out = []
     for N in sizes:
         Xs, lam, E = _paper_gaussian(N, 100, 9000 + N)
@@ -752,30 +783,46 @@ def run_convergence(a):
             dl = ctx.cd_sweep(sel) if len(sel) else 0.0
             return dl + ctx.field_sweep()
 
-        run("cd", {"fn": cd}, 60)
+        run("cd", {"fn": cd}, cd_iters)
         for kappa in (0.25, 1.0, 4.0):
             run(f"gcd_screen_kappa{kappa:g}", {"fn": lambda c, k=kappa: c.gcd_step(1, k)[0],
-                                                 "opts": {"knn_mode": R.RECON_KNN_SCREEN}}, 400)
-        run("gcd_nndescent_kappa1", {"fn": lambda c: c.gcd_step(1, 1.0)[0]}, 400)
+                                                 "opts": {"knn_mode": R.RECON_KNN_SCREEN}}, gcd_iters)
+        run("gcd_nndescent_kappa1", {"fn": lambda c: c.gcd_step(1, 1.0)[0]}, gcd_iters)
         best = max(v[-1][1] for k, v in res.items() if isinstance(v, list))
         tol = 1e-6 * abs(best)
         res["time_to_optimum"] = {k: next((t for t, o in v if o >= best - tol), None)
                                   for k, v in res.items() if isinstance(v, list)}
         res["iterations"] = {k: len(v) - 1 for k, v in res.items() if isinstance(v, list)}
-        print(json.dumps({"N": N, "time_to_optimum": res["time_to_optimum"], "iterations": res["iterations"],
-                          "objective_best": best}), flush=True)
+        res["objective_best"] = best
         for k in list(res):
             if isinstance(res[k], list) and len(res[k]) > 40:  # keep the line short
                 v = res[k]
                 res[k] = v[:: max(1, len(v) // 40)] + [v[-1]]
         out.append(res)
-    print(json.dumps({"convergence": out, "M": 100}), flush=True)
+    return {"convergence": out, "M": 100}
+
+
+def run_convergence(a):
+    import torch
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2401_01404_gb300 import recon as R
+
+    res = _convergence(R, a.convergence or [100, 1000, 10000], torch.cuda.current_stream())
+    for r in res["convergence"]:
+        print(json.dumps({"N": r["N"], "time_to_optimum": r["time_to_optimum"], "iterations": r["iterations"],
+                          "objective_best": r["objective_best"]}), flush=True)
+    print(json.dumps(res), flush=True)
 
 
 def main():
     a = _args()
     if a.peaks:
         run_peaks(a)
+        return
+    if a.gcd_step:
+        run_gcd_step(a)
         return
     if a.screen_bench:
         run_screen_bench(a)

@@ -113,7 +113,16 @@ typedef struct {
                              sample of a node has the same field) the screen still uses the
                              general form above; by default it computes the spin product
                              X X^T in E4M3 (exact, K = M) plus a rank-two correction */
-    int32_t reserved[2];  /* zero */
+    /* A split search: with shard_count > 1 this context's screen covers only shard
+     * shard_index of its units (every shard_count-th 128 x 256 block of the pair
+     * matrix), so that shard_count processes (one GPU each) share one search.  Each
+     * returns the m best pairs of its shard (stored couplings included), and
+     * recon_select_best over the union of the shards' results gives the unsharded
+     * answer exactly.  Only with RECON_KNN_SCREEN (else RECON_EUNSUPPORTED);
+     * recon_gcd_step refuses a sharded context (merge before updating); 0 or 1:
+     * no sharding. */
+    int32_t shard_index;
+    int32_t shard_count;
 } recon_options;
 
 typedef struct {
@@ -199,6 +208,20 @@ recon_status recon_score(recon_ctx *ctx, const int32_t *pairs, int64_t P, float 
  * Synchronous. */
 recon_status recon_best_pairs(recon_ctx *ctx, int32_t k, double kappa, int32_t *pairs, float *d,
                               int64_t cap, int64_t *m_out, int32_t out_is_device);
+
+/* recon_select_best -- the m best of P scored pairs, unique and ordered by
+ * (d, i, j): the last step of Algorithm 3 (the best m of the pairs its levels
+ * collected), here the merge of the shards of a split search (see
+ * recon_options.shard_count).  Duplicate pairs must carry the same d (as the
+ * same pair scored at the same state does) and are kept once.
+ *   pairs : P x 2 int32, i != j, both in [0, N) (either order); d: P floats.
+ *   out_pairs : cap x 2 int32 (canonical i < j), out_d: cap floats (may be NULL);
+ *   *count_out = min(m, unique pairs); when cap < that, nothing is written and
+ *   RECON_EINVAL is returned.  io_is_device: all four arrays on the device (else
+ *   host).  Synchronous. */
+recon_status recon_select_best(recon_ctx *ctx, const int32_t *pairs, const float *d, int64_t P, int64_t m,
+                               int32_t *out_pairs, float *out_d, int64_t cap, int64_t *count_out,
+                               int32_t io_is_device);
 
 /* recon_score_noalloc -- recon_score for host pair lists that performs no
  * device allocation (the paper has no counterpart: this is a deployment

@@ -274,6 +274,11 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
         return set_err(nullptr, RECON_EINVAL, "unknown distance");
     if (o.distance == RECON_DIST_GRADIENT && o.knn_mode == RECON_KNN_SCREEN)
         return set_err(nullptr, RECON_EUNSUPPORTED, "the gradient distance ranks pairs the screen does not keep");
+    if (o.shard_count < 0 || (o.shard_count > 1 && (o.shard_index < 0 || o.shard_index >= o.shard_count)))
+        return set_err(nullptr, RECON_EINVAL, "shard_index %d outside [0, shard_count = %d)", o.shard_index,
+                       o.shard_count);
+    if (o.shard_count > 1 && o.knn_mode != RECON_KNN_SCREEN)
+        return set_err(nullptr, RECON_EUNSUPPORTED, "a sharded search needs RECON_KNN_SCREEN");
     if (o.screen_fp8 && model != RECON_ISING)
         return set_err(nullptr, RECON_EUNSUPPORTED, "fp8 screen operands are for the Ising model only");
     if (!(o.learned_frac >= 0.f && o.learned_frac <= 1.f))
@@ -441,6 +446,43 @@ extern "C" recon_status recon_exhaustive_best(recon_ctx *c, int64_t m, int32_t *
     return RECON_OK;
 }
 
+extern "C" recon_status recon_select_best(recon_ctx *c, const int32_t *pairs, const float *d, int64_t P, int64_t m,
+                                          int32_t *out_pairs, float *out_d, int64_t cap, int64_t *count_out,
+                                          int32_t io_is_device) {
+    LIVE(c);
+    if (!count_out) return set_err(c, RECON_EINVAL, "count_out is NULL");
+    *count_out = 0;
+    if (P < 0 || m < 0) return set_err(c, RECON_EINVAL, "P or m < 0");
+    if (P > 0 && (!pairs || !d)) return set_err(c, RECON_EINVAL, "pairs or d is NULL");
+    if (P == 0 || m == 0) return RECON_OK;
+    const int32_t *pin = pairs;
+    const float *din = d;
+    if (!io_is_device) {
+        ENSURE(BUF_TMP0, sizeof(int32_t) * 2 * P);
+        ENSURE(BUF_TMP1, sizeof(float) * P);
+        CK(cudaMemcpyAsync(c->bufs[BUF_TMP0].p, pairs, sizeof(int32_t) * 2 * P, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->bufs[BUF_TMP1].p, d, sizeof(float) * P, cudaMemcpyHostToDevice, c->stream));
+        pin = buf<int32_t>(c, BUF_TMP0);
+        din = buf<float>(c, BUF_TMP1);
+    }
+    int32_t *pd = nullptr;
+    float *dd = nullptr;
+    int64_t n = 0;
+    recon_status st = select_run(c, pin, din, P, m, &pd, &dd, &n);
+    if (st != RECON_OK) {
+        if (st == RECON_EINVAL) return set_err(c, RECON_EINVAL, "a pair has an id outside [0, N) or i == j");
+        return st;
+    }
+    if (cap < n || !out_pairs) {
+        *count_out = n;
+        return set_err(c, RECON_EINVAL, "cap %lld < %lld selected pairs", (long long)cap, (long long)n);
+    }
+    st = deliver_pairs(c, pd, dd, n, out_pairs, out_d, io_is_device);
+    if (st != RECON_OK) return st;
+    *count_out = n;
+    return RECON_OK;
+}
+
 extern "C" recon_status recon_row_best(recon_ctx *c, const int32_t *rows, int64_t nrows, float d_cut, int32_t *pairs,
                                        float *d, int64_t cap, int64_t *count_out) {
     LIVE(c);
@@ -592,6 +634,9 @@ extern "C" recon_status recon_knn_graph(recon_ctx *c, int32_t *ids, float *d, in
 extern "C" recon_status recon_gcd_step(recon_ctx *c, int32_t k, double kappa, double *delta_out,
                                        double *objective_out, int64_t *m_out) {
     LIVE(c);
+    if (c->opt.shard_count > 1)
+        return set_err(c, RECON_EUNSUPPORTED, "a sharded context returns its shard's best pairs; merge them "
+                                              "(recon_select_best) before the updates");
     if (k < 1) return set_err(c, RECON_EINVAL, "k = %d < 1", k);
     if (!(kappa > 0.0) || !std::isfinite(kappa)) return set_err(c, RECON_EINVAL, "kappa must be > 0");
     const int64_t m = std::min<int64_t>(round_half_up(kappa * (double)c->N), c->N * (c->N - 1) / 2);

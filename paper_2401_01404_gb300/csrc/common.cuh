@@ -422,11 +422,12 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
 // k_valid are nonzero; threshold `thr` on |G_ij|, margin rel * (l_i + l_j) (or l_i l_j) + abs_margin
 // when l1 is given, stored couplings skipped when skip_stored
 // r1 != NULL: the rank-one form at the empty network (A = B the E4M3 spin rows, r1 the
-// per-node (s_i, tau_i); keep |2 S_ij - tau_j s_i - tau_i s_j| > thr - abs_margin)
+// per-node (s_i, tau_i); keep |2 S_ij - tau_j s_i - tau_i s_j| > thr - abs_margin);
+// use_shard: cover only the context's shard of the units (options.shard_index / shard_count)
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
                              unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
-                             int k_valid, const float2 *r1);
+                             int k_valid, const float2 *r1, bool use_shard);
 int screen_k_rank1(recon_ctx *c);
 float screen_rank1_margin(recon_ctx *c);
 cudaError_t launch_screen_prep_rank1(recon_ctx *c, void *A, float2 *r1, unsigned long long *flag);

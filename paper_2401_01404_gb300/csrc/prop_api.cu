@@ -367,7 +367,7 @@ recon_status learned_seed_lists(recon_ctx *c, int n, int K, const int32_t *klen,
         CK(grow(P.s_cands, sizeof(int32_t) * 2 * cap, c->stream));
         CK(cudaMemsetAsync(c->cnt + CNT_SCRATCH3, 0, sizeof(unsigned long long), c->stream));
         CK(launch_screen_ex(c, P.seedA.p, P.seedA.p, 64, thr, nullptr, 0.f, 0, false, (int32_t *)P.s_cands.p, cap,
-                            c->cnt + CNT_SCRATCH3, nullptr, false, 0.f, 64, nullptr));
+                            c->cnt + CNT_SCRATCH3, nullptr, false, 0.f, 64, nullptr, false));
         CK(cudaMemcpyAsync(c->cnt_host + CNT_SCRATCH3, c->cnt + CNT_SCRATCH3, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));

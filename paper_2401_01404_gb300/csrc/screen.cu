@@ -229,6 +229,8 @@ struct ScreenArgs {
     unsigned long long *count;
     unsigned long long *err;
     int stall;          // fault injection: issue no loads, so the bounded waits run out
+    int shard, nshard;  // this launch covers units shard, shard + nshard, ... (a shard of the screen)
+    int64_t nlocal;     // units of this shard
 };
 
 template <bool F8, bool R1>
@@ -271,9 +273,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         if (lane == 0) {  // TMA producer
             UnitWalker walk(a.T);
             int64_t kb_all = 0;
-            for (int64_t t = blockIdx.x; t < a.ntiles && !a.stall && !*(volatile int *)abort; t += gridDim.x) {
+            for (int64_t t = blockIdx.x; t < a.nlocal && !a.stall && !*(volatile int *)abort; t += gridDim.x) {
                 int ra, rb;
-                walk.map(t, ra, rb);
+                walk.map(a.shard + a.nshard * t, ra, rb);
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
                     const int s = (int)(kb_all % STAGES);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
             int64_t kb_all = 0, it = 0, last_it = -1;  // last_it: the unit of the last accumulator commit
-            for (int64_t t = blockIdx.x; t < a.ntiles && !*(volatile int *)abort; t += gridDim.x, ++it) {
+            for (int64_t t = blockIdx.x; t < a.nlocal && !*(volatile int *)abort; t += gridDim.x, ++it) {
                 const int b = (int)(it & 1);
                 if (!mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
                 tc_fence_after();
@@ -439,13 +441,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         int ra = 0, jt = 0;
         float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
         float2 li_n = make_float2(0.f, 0.f);
-        if ((int64_t)blockIdx.x < a.ntiles) {
-            walk.map(blockIdx.x, ra, jt);
+        if ((int64_t)blockIdx.x < a.nlocal) {
+            walk.map(a.shard + a.nshard * (int64_t)blockIdx.x, ra, jt);
             load_norms(jt, n0, n1);
             li_n = load_row(ra);
         }
         int64_t it = 0;
-        for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+        for (int64_t t = blockIdx.x; t < a.nlocal; t += gridDim.x, ++it) {
             const int b = (int)(it & 1);
             const int i = ra + 32 * rg + lane;
             const int jt_cur = jt + (BN / 2) * ch;
@@ -484,8 +486,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             }
             const float ui = li, vi = li_n.y;
             // the next unit's mapping and norms, in flight during this unit's compare
-            if (t + gridDim.x < a.ntiles) {
-                walk.map(t + gridDim.x, ra, jt);
+            if (t + gridDim.x < a.nlocal) {
+                walk.map(a.shard + a.nshard * (t + gridDim.x), ra, jt);
                 load_norms(jt, n0, n1);
                 li_n = load_row(ra);
             }
@@ -795,7 +797,7 @@ float screen_acc_err(recon_ctx *c, bool fp8) {
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
                              unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
-                             int k_valid, const float2 *r1) {
+                             int k_valid, const float2 *r1, bool use_shard) {
     if (r1 && !fp8) return cudaErrorInvalidValue;  // the rank-one form reads E4M3 spins
     const int bke = fp8 ? BK8 : BK;  // elements per 128-byte k-block row
     const int kchunk = fp8 ? 32 : 16;  // elements per MMA
@@ -851,7 +853,11 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.count = count;
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
-    const int64_t grid = std::min<int64_t>(a.ntiles, (int64_t)c->num_sms);  // persistent: one CTA per SM
+    // a shard of the screen: every nshard-th unit, starting at unit `shard`
+    a.nshard = use_shard && c->opt.shard_count > 1 ? c->opt.shard_count : 1;
+    a.shard = a.nshard > 1 ? c->opt.shard_index : 0;
+    a.nlocal = a.ntiles > a.shard ? (a.ntiles - a.shard + a.nshard - 1) / a.nshard : 0;
+    const int64_t grid = std::min<int64_t>(a.nlocal, (int64_t)c->num_sms);  // persistent: one CTA per SM
     const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
     if (r1)
         k_screen<true, true><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
@@ -860,7 +866,7 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     else
         k_screen<false, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
     note_launch();
-    if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.ntiles;
+    if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.nlocal;
     return cudaGetLastError();
 }
 
@@ -868,5 +874,5 @@ cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const floa
                           unsigned long long *count, float margin_scale, double *flop_out, bool fp8) {
     return launch_screen_ex(c, A, B, screen_k(c, fp8), (float)c->opt.lambda, l1, margin_scale,
                             c->model == RECON_GAUSSIAN, true, out, cap, count, flop_out, fp8, 0.f,
-                            2 * (int)c->Mp, nullptr);
+                            2 * (int)c->Mp, nullptr, true);
 }

@@ -685,6 +685,19 @@ __global__ void k_unique_gather(int64_t P, int64_t m, const uint32_t *perm, cons
     outd[pos[q]] = dd[a];
 }
 
+// canonical copy (i < j) of a scored pair list; ids outside [0, n) or i == j
+// raise ERR_BAD_VALUE
+__global__ void k_canon_pairs(int64_t P, int n, const int32_t *in, const float *din, int32_t *out, float *dout,
+                              unsigned long long *cnt) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P) return;
+    const int a = in[2 * q], b = in[2 * q + 1];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_BAD_VALUE);
+    out[2 * q] = a < b ? a : b;
+    out[2 * q + 1] = a < b ? b : a;
+    dout[q] = din[q];
+}
+
 __global__ void k_iota(int32_t *p, int64_t n) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) p[e] = (int32_t)e;
@@ -1570,7 +1583,7 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
         if (rank1)
             CKS(launch_screen_ex(c, S.scr_A.p, S.scr_A.p, screen_k_rank1(c), (float)c->opt.lambda, nullptr, 0.f, 0,
                                  true, (int32_t *)S.cand.p, cap, counter(c, CNT_SCRATCH1), &flop, true,
-                                 screen_rank1_margin(c), (int)c->Mp, (const float2 *)S.scr_l1.p));
+                                 screen_rank1_margin(c), (int)c->Mp, (const float2 *)S.scr_l1.p, true));
         else
             CKS(launch_screen(c, S.scr_A.p, S.scr_B.p, (float *)S.scr_l1.p, (int32_t *)S.cand.p, cap,
                               counter(c, CNT_SCRATCH1), rel, &flop, fp8));
@@ -1609,6 +1622,29 @@ recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_
     }
     S.res_n = P;
     recon_status st = finish_results(c, m, count);
+    if (st != RECON_OK) return st;
+    *pairs_dev = (int32_t *)S.out_pairs.p;
+    *d_dev = (float *)S.out_d.p;
+    return RECON_OK;
+}
+
+// the m best of a scored pair list (device), unique, ordered by (d, i, j):
+// the merge of the shards of a split search
+recon_status select_run(recon_ctx *c, const int32_t *pairs, const float *d, int64_t P, int64_t m, int32_t **pairs_dev,
+                        float **d_dev, int64_t *count) {
+    SearchBufs &S = SB(c);
+    S.res_n = 0;
+    S.g0_K = 0;
+    GROW(S.res_pairs, sizeof(int32_t) * 2 * std::max<int64_t>(P, 1));
+    GROW(S.res_d, sizeof(float) * std::max<int64_t>(P, 1));
+    k_canon_pairs<<<nblk(P), 256, 0, c->stream>>>(P, (int)c->N, pairs, d, (int32_t *)S.res_pairs.p,
+                                                  (float *)S.res_d.p, c->cnt);
+    note_launch();
+    CKS(cudaGetLastError());
+    recon_status st = check_err_flags(c, "select");
+    if (st != RECON_OK) return st;
+    S.res_n = P;
+    st = finish_results(c, m, count);
     if (st != RECON_OK) return st;
     *pairs_dev = (int32_t *)S.out_pairs.p;
     *d_dev = (float *)S.out_d.p;

@@ -52,6 +52,8 @@ recon_status score_pairs_device(recon_ctx *c, const int32_t *pairs, int64_t P, c
 recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
 recon_status screen_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
 recon_status exhaustive_run(recon_ctx *c, int64_t m, int32_t **pairs_dev, float **d_dev, int64_t *count);
+recon_status select_run(recon_ctx *c, const int32_t *pairs, const float *d, int64_t P, int64_t m, int32_t **pairs_dev,
+                        float **d_dev, int64_t *count);
 recon_status row_best_run(recon_ctx *c, const int32_t *rows_dev, int64_t nrows, float cut, int32_t **pairs_dev,
                           float **d_dev, int64_t *count);
 recon_status knn_graph_copy(recon_ctx *c, int32_t *ids, float *d, int64_t cap, int32_t *k_out, int64_t *n_out);

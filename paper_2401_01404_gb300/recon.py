@@ -31,7 +31,7 @@ class recon_options(C.Structure):
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
                 ("timing", C.c_int32), ("no_graphs", C.c_int32),
                 ("learned_frac", C.c_float), ("distance", C.c_int32), ("screen_fp8", C.c_int32),
-                ("screen_no_rank1", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("screen_no_rank1", C.c_int32), ("shard_index", C.c_int32), ("shard_count", C.c_int32)]
 
 
 class recon_stats(C.Structure):
@@ -72,6 +72,8 @@ _EXPORTS = {
     "recon_objective": (C.c_int, [C.c_void_p, C.c_void_p]),
     "recon_score": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32]),
     "recon_score_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "recon_select_best": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int32]),
     "recon_best_pairs": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_void_p, C.c_int64,
                                    C.c_void_p, C.c_int32]),
     "recon_exhaustive_best": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -213,6 +215,22 @@ def recon_best_pairs(ctx, k: int, kappa: float, N: int):
     mo = C.c_int64()
     _check(lib().recon_best_pairs(ctx, k, float(kappa), pairs.ctypes.data, d.ctypes.data, cap, C.byref(mo), 0), ctx)
     return pairs[:mo.value], d[:mo.value]
+
+
+def recon_select_best(ctx, pairs, d, m: int):
+    """The m best of a scored pair list (host arrays), unique and ordered by
+    (d, i, j): (pairs [n x 2], d [n])."""
+    p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    dd = np.ascontiguousarray(np.asarray(d, dtype=np.float32).ravel())
+    if len(dd) != len(p):
+        raise ValueError("pairs and d differ in length")
+    cap = min(int(m), len(p))
+    out = np.empty((max(cap, 1), 2), dtype=np.int32)
+    od = np.empty(max(cap, 1), dtype=np.float32)
+    n = C.c_int64(0)
+    _check(lib().recon_select_best(ctx, p.ctypes.data, dd.ctypes.data, len(p), int(m), out.ctypes.data, od.ctypes.data,
+                                   cap, C.byref(n), 0), ctx)
+    return out[:n.value], od[:n.value]
 
 
 def recon_exhaustive_best(ctx, m: int, N: int):
