@@ -258,6 +258,9 @@ def _c2_leg(R, stream, peaks, steps, workload="ising_n2000_m1000", recall=True):
     score_pairs = s1["score_pairs"] - s0["score_pairs"]
     launches = s1["score_launches"] - s0["score_launches"]
     rate = score_pairs * wl.M / (score_ms / 1e3) if score_ms else None
+    # Newton passes (sample passes beyond the first) per scored pair, over the whole step
+    evals = s1["pair_evals"] - s0["pair_evals"]
+    passes_per_pair = (s1["newton_passes"] - s0["newton_passes"]) / max(evals, 1)
     out = {"workload": wl.name, "N": wl.N, "M": wl.M, "k": k, "kappa": kappa, "lambda": round(lam, 4),
            "gcd_step": {"pair_sample_evals_per_s": (s1["pair_evals"] - s0["pair_evals"]) * wl.M / t,
                         "ms_per_step": t / steps * 1e3, "steps": steps,
@@ -273,12 +276,21 @@ def _c2_leg(R, stream, peaks, steps, workload="ising_n2000_m1000", recall=True):
             out["scorer"]["roofline_l2"] = {"bound": "l2", "achieved": rate * 4.125 / 1e9, "peak": l2, "unit": "GB/s",
                                             "frac": rate * 4.125 / 1e9 / l2,
                                             "peak_source": "measured (recon_device_peaks, L2-resident reads)"}
+        out["scorer"]["newton_passes_per_pair"] = passes_per_pair
         if fp32:
-            # 3 FP32 ops per pair-sample in the first pass; the peak counts an FMA as 2 flops
-            ops = rate * 3.0
+            # 3 FP32 ops per pair-sample in the first pass, about 12 more per Newton pass;
+            # the peak counts an FMA as 2 flops
+            ops = rate * (3.0 + 12.0 * passes_per_pair)
             out["scorer"]["roofline_alu"] = {"bound": "alu", "achieved": ops / 1e12, "peak": fp32 / 2.0,
                                              "unit": "Tops/s (FP32 instructions)", "frac": ops / 1e12 / (fp32 / 2.0),
                                              "peak_source": "measured (recon_device_peaks, FMA rate / 2)"}
+        mufu = peaks.get("mufu_rcp_gops")
+        if mufu:
+            # two reciprocals (MUFU) per pair-sample per Newton pass
+            ops = rate * 2.0 * passes_per_pair
+            out["scorer"]["roofline_mufu"] = {"bound": "mufu", "achieved": ops / 1e9, "peak": mufu,
+                                              "unit": "Gops/s (rcp.approx)", "frac": ops / 1e9 / mufu,
+                                              "peak_source": "measured (recon_device_peaks, rcp.approx rate)"}
     if not recall:
         return out
     # time to 0.99 recall against the exhaustive exact best pairs
@@ -309,6 +321,24 @@ def _c2_leg(R, stream, peaks, steps, workload="ising_n2000_m1000", recall=True):
         t_hit, curve = _nnd_curve(R, X_dev, wl, lam, kk, kappa, stream, range(1, 13), rec)
         out["time_to_recall"][f"plain_fp32_k{kk}_s"] = t_hit
         out["time_to_recall"][f"plain_fp32_k{kk}_curve"] = [c[:3] for c in curve]
+    # the learned proposal, trained (untimed) on another planted graph of the same
+    # kind, seeding the first lists; recall against time next to random lists
+    tp = time.perf_counter()
+    other = inputs.ising_workload(wl.name + "_pretrain", wl.N, wl.M, "regular", 4, "pm", 0.3, 0.0, 300, 4242, k, kappa,
+                                  "cuda")
+    tr = R.Recon(other.samples_major(), R.RECON_ISING, stream=stream, lam=lam)
+    losses = R.recon_proposal_train(tr.ctx, steps=1500, lr=3e-3, seed=7)
+    weights = R.recon_proposal_weights(tr.ctx)
+    tr.close()
+    t_pre = time.perf_counter() - tp
+    _, c_learn = _nnd_curve(R, X_dev, wl, lam, k, kappa, stream, range(1, 9), rec, seed_mode=R.RECON_SEED_LEARNED,
+                            weights=weights)
+    _, c_rand = _nnd_curve(R, X_dev, wl, lam, k, kappa, stream, range(1, 9), rec)
+    out["time_to_recall"]["learned_fp32_k16_curve"] = [c[:3] for c in c_learn]
+    out["time_to_recall"]["learned_recall_gain_over_random"] = [round(b[2] - a_[2], 5) for a_, b in zip(c_rand, c_learn)]
+    out["time_to_recall"]["learned_pretrain"] = {"seconds": round(t_pre, 2), "steps": 1500,
+                                                 "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                                                 "data": "another planted 4-regular graph (Omega redrawn per step)"}
     return out
 
 
@@ -469,7 +499,7 @@ def run_ours(a):
         pre = inputs.ising_workload(wl.name + "_pretrain", 100000, wl.M, "er", 5, "normal", 0.3, 0.0, 300, 4243, k,
                                     kappa, "cuda")
         tr = R.Recon(pre.samples_major(), R.RECON_ISING, stream=stream, lam=inputs.default_lambda(100000, wl.M, 2.0))
-        losses = R.recon_proposal_train(tr.ctx, steps=400, lr=3e-3, seed=7)
+        losses = R.recon_proposal_train(tr.ctx, steps=1000, lr=3e-3, seed=7)
         weights = R.recon_proposal_weights(tr.ctx)
         tr.close()
         t_pre = time.perf_counter() - tp

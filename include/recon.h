@@ -325,7 +325,11 @@ typedef struct {
     int64_t n_best;         /* n_pairs == 0: train on the n_best exact best pairs (tensor-core
                                screen, default N) ... */
     int64_t n_random;       /* ... and n_random uniform random pairs (default 8N) */
-    int32_t reserved[8];
+    int32_t fixed_sketch;   /* nonzero: train on the context's own sketches; by default Omega
+                               is drawn afresh at every step, so that the network learns a
+                               function of sketch similarity that carries to other data,
+                               rather than the nodes of its training data */
+    int32_t reserved[7];
 } recon_train_opts;
 
 /* Parameters: W1 [128 x 64] | b1 [128] | W2 [32 x 128] | b2 [32], row-major, FP32

@@ -198,13 +198,11 @@ static recon_status build_state(recon_ctx *c, const void *X, int x_is_device) {
     const int64_t N = c->N, M = c->M;
     const size_t esz = c->model == RECON_ISING ? 1 : 4;
     const size_t xbytes = (size_t)N * M * esz;
-    c->x_host.resize(xbytes);
+    // the samples are kept only in the device layout (checkpoints unpack them)
     void *Xd = nullptr;
     if (x_is_device) {
-        CK(cudaMemcpyAsync(c->x_host.data(), X, xbytes, cudaMemcpyDeviceToHost, c->stream));
         Xd = const_cast<void *>(X);
     } else {
-        memcpy(c->x_host.data(), X, xbytes);
         ENSURE(BUF_TMP0, xbytes);
         Xd = c->bufs[BUF_TMP0].p;
         CK(cudaMemcpyAsync(Xd, X, xbytes, cudaMemcpyHostToDevice, c->stream));
@@ -848,13 +846,23 @@ extern "C" recon_status recon_save(recon_ctx *c, const char *path) {
     recon_stats s{};
     st = recon_get_stats(c, &s);
     if (st != RECON_OK) return st;
+    // the samples, sample-major as recon_init took them, rebuilt from the device layout
+    const size_t xbytes = (size_t)c->N * c->M * (c->model == RECON_ISING ? 1 : 4);
+    std::vector<uint8_t> xs(xbytes);
+    ENSURE(BUF_TMP0, xbytes);
+    if (c->model == RECON_ISING)
+        CK(launch_ising_unpack(c->iv(), buf<int8_t>(c, BUF_TMP0), c->stream));
+    else
+        CK(launch_gauss_unpack(c->gv(), buf<float>(c, BUF_TMP0), c->stream));
+    CK(cudaMemcpyAsync(xs.data(), c->bufs[BUF_TMP0].p, xbytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     FILE *f = fopen(path, "wb");
     if (!f) return set_err(c, RECON_EINVAL, "cannot open %s for writing", path);
     int64_t hdr[4] = {c->model, c->N, c->M, nnz};
     bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, sizeof hdr, 1, f) == 1 &&
               fwrite(&c->opt, sizeof c->opt, 1, f) == 1 && fwrite(&s, sizeof s, 1, f) == 1 &&
               fwrite(&c->stats_calls, sizeof c->stats_calls, 1, f) == 1 &&
-              fwrite(c->x_host.data(), 1, c->x_host.size(), f) == c->x_host.size() &&
+              fwrite(xs.data(), 1, xs.size(), f) == xs.size() &&
               fwrite(fields.data(), sizeof(float), c->N, f) == (size_t)c->N &&
               (nnz == 0 || (fwrite(ij.data(), sizeof(int32_t), 2 * nnz, f) == (size_t)(2 * nnz) &&
                             fwrite(w.data(), sizeof(float), nnz, f) == (size_t)nnz));

@@ -258,8 +258,6 @@ struct recon_ctx {
     float *phi = nullptr, *t = nullptr, *h = nullptr, *H = nullptr;
     // Gaussian
     float *xg = nullptr, *e = nullptr, *mu = nullptr, *s2 = nullptr, *Q = nullptr;
-    // host copy of the samples (sample-major), kept for checkpoints
-    std::vector<uint8_t> x_host;
     // per-node list lengths of the first FindBest level (empty: uniform k)
     std::vector<int32_t> klen_host;
 
@@ -357,6 +355,7 @@ cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int3
                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
                                 unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_ising_field_sweep(IsingView v, ScoreParams p, double *delta, cudaStream_t s);
+cudaError_t launch_ising_unpack(IsingView v, int8_t *X_sm, cudaStream_t s);
 int ising_max_words();
 
 // gauss.cu
@@ -377,6 +376,7 @@ cudaError_t launch_gauss_update(GaussView v, WTable W, ScoreParams p, const int3
                                 const int32_t *order, int64_t begin, int64_t end, double *delta,
                                 unsigned long long *cnt, cudaStream_t s);
 cudaError_t launch_gauss_diag_sweep(GaussView v, double *delta, cudaStream_t s);
+cudaError_t launch_gauss_unpack(GaussView v, float *X_sm, cudaStream_t s);
 
 // util.cu
 cudaError_t launch_penalty(WTable W, double *out, cudaStream_t s);

@@ -302,6 +302,21 @@ inline unsigned grid_for(int64_t warps, int threads = 256) {
 
 }  // namespace
 
+// the samples back in the API's sample-major layout (checkpoints)
+__global__ void k_gunpack(GaussView v, float *X_sm) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)v.N * v.M) return;
+    const int64_t m = e / v.N, i = e - m * v.N;
+    X_sm[e] = v.xg[i * v.Mp + m];
+}
+
+cudaError_t launch_gauss_unpack(GaussView v, float *X_sm, cudaStream_t s) {
+    const int64_t n = (int64_t)v.N * v.M;
+    k_gunpack<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, X_sm);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gauss_pack(const float *X_sm, int64_t M, int64_t N, int Mp, float *xg, unsigned long long *cnt,
                               cudaStream_t s) {
     int64_t n = N * (int64_t)Mp;

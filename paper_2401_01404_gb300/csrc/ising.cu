@@ -1041,6 +1041,21 @@ cudaError_t launch_ising_score_seg(IsingView v, WTable W, ScoreParams p, const i
     return cudaGetLastError();
 }
 
+// the spins back in the API's sample-major int8 layout (checkpoints)
+__global__ void k_unpack_spins(IsingView v, int8_t *X_sm) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)v.N * v.M) return;
+    const int64_t m = e / v.N, i = e - m * v.N;
+    X_sm[e] = ((v.xbits[i * v.Mw + (m >> 5)] >> (m & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
+}
+
+cudaError_t launch_ising_unpack(IsingView v, int8_t *X_sm, cudaStream_t s) {
+    const int64_t n = (int64_t)v.N * v.M;
+    k_unpack_spins<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, X_sm);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ising_update(IsingView v, WTable W, ScoreParams p, const int32_t *pairs, const int32_t *order,
                                 int64_t begin, int64_t end, double *delta, unsigned long long *cnt,
                                 cudaStream_t s) {

@@ -318,9 +318,11 @@ extern "C" recon_status recon_proposal_train(recon_ctx *c, const recon_train_opt
     }
     CK(grow(P.loss, sizeof(double) * (o.steps + 1), c->stream));
     for (int s = 0; s < o.steps; ++s) {
+        if (!o.fixed_sketch) CK(proposal_resketch(c, P, mix64(P.omega_seed ^ mix64(0x51ce7c4ull + (uint64_t)P.t))));
         CK(proposal_grad(c, P, (int32_t *)P.tpairs.p, (float *)P.ttau.p, n, (double *)P.loss.p + s));
         CK(proposal_adam(c, P, o.lr));
     }
+    if (!o.fixed_sketch) CK(proposal_resketch(c, P, P.omega_seed));  // the context's own sketches again
     if (loss_out && o.steps > 0) {
         std::vector<double> l(o.steps);
         CK(cudaMemcpyAsync(l.data(), P.loss.p, sizeof(double) * o.steps, cudaMemcpyDeviceToHost, c->stream));

@@ -15,7 +15,11 @@
 //   training: full-batch Adam over the given pairs, gradients by hand-written
 //           backward kernels (a per-node pass for the hidden-layer gradient,
 //           then the weight gradients as sums of outer products over nodes,
-//           accumulated in registers per block)
+//           accumulated in registers per block).  Omega is drawn afresh at every
+//           step unless asked otherwise: with a fixed Omega the network can learn
+//           the nodes of its training data from their sketches (and carries
+//           nothing to other data); with a new Omega per step only a function of
+//           the sketches' similarity lowers the loss, and it holds for any Omega
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -274,6 +278,17 @@ cudaError_t proposal_setup(recon_ctx *c, Proposal &P, uint64_t seed) {
     k_to_bf16<<<nb(E * H), 256, 0, st>>>(E * H, (float *)P.w.p + H * S + H, (__nv_bfloat16 *)P.w2b.p);
     note_launch();
     k_omega<<<nb((int64_t)S * c->Mw), 256, 0, st>>>((int)c->M, (int)c->Mw, P.omega_seed, (uint32_t *)P.omega.p);
+    note_launch();
+    k_sketch<<<nb(c->N * S), 256, 0, st>>>(c->iv(), (uint32_t *)P.omega.p, (float *)P.sketch.p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Omega drawn from `seed` and the sketches recomputed with it (training redraws
+// Omega at every step; the context's own Omega comes from P.omega_seed)
+cudaError_t proposal_resketch(recon_ctx *c, Proposal &P, uint64_t seed) {
+    cudaStream_t st = c->stream;
+    k_omega<<<nb((int64_t)S * c->Mw), 256, 0, st>>>((int)c->M, (int)c->Mw, seed, (uint32_t *)P.omega.p);
     note_launch();
     k_sketch<<<nb(c->N * S), 256, 0, st>>>(c->iv(), (uint32_t *)P.omega.p, (float *)P.sketch.p);
     note_launch();

@@ -25,6 +25,7 @@ struct Proposal {
 int64_t proposal_param_count();
 cudaError_t proposal_setup(recon_ctx *c, Proposal &P, uint64_t seed);
 cudaError_t proposal_forward(recon_ctx *c, Proposal &P, bool keep_act);
+cudaError_t proposal_resketch(recon_ctx *c, Proposal &P, uint64_t seed);
 cudaError_t proposal_grad(recon_ctx *c, Proposal &P, const int32_t *pairs, const float *tau, int64_t n,
                           double *loss_dev);
 cudaError_t proposal_adam(recon_ctx *c, Proposal &P, float lr);

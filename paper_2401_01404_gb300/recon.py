@@ -55,7 +55,7 @@ class recon_peaks(C.Structure):
 class recon_train_opts(C.Structure):
     _fields_ = [("steps", C.c_int32), ("lr", C.c_float), ("seed", C.c_uint64), ("n_pairs", C.c_int64),
                 ("pairs", C.c_void_p), ("targets", C.c_void_p), ("n_best", C.c_int64), ("n_random", C.c_int64),
-                ("reserved", C.c_int32 * 8)]
+                ("fixed_sketch", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class ReconError(RuntimeError):
@@ -339,11 +339,12 @@ def recon_proposal_param_count() -> int:
 
 
 def recon_proposal_train(ctx, steps: int = 300, lr: float = 3e-3, seed: int = 7, pairs=None, targets=None,
-                         n_best: int = 0, n_random: int = 0):
+                         n_best: int = 0, n_random: int = 0, fixed_sketch: int = 0):
     """Trains the learned proposal; returns the loss before each step."""
     o = recon_train_opts()
     lib().recon_default_train_opts(C.byref(o))
     o.steps, o.lr, o.seed, o.n_best, o.n_random = steps, lr, seed, n_best, n_random
+    o.fixed_sketch = fixed_sketch
     keep = []
     if pairs is not None:
         p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))

@@ -110,3 +110,22 @@ def test_gauss_findbest_exact_knn(R):
     p1, d1 = ctx.best_pairs(4, 1.0)
     p2, d2 = ctx.exhaustive_best(N)
     assert np.array_equal(np.sort(d1), np.sort(d2))
+
+
+def test_gaussian_checkpoint_roundtrip(R, tmp_path):
+    """A checkpoint of the Gaussian model (samples rebuilt from the device
+    layout) loads into a context that continues exactly as the saved one."""
+    X = inputs.gaussian_torus_samples(6, 7, -0.2, 1.8, 150, 4000).astype(np.float32)
+    N = X.shape[0]
+    ctx = R.Recon(np.ascontiguousarray(X.T), R.RECON_GAUSSIAN, lam=0.5, knn_mode=R.RECON_KNN_EXHAUSTIVE)
+    ctx.gcd_step(4, 1.0)
+    path = str(tmp_path / "g.bin")
+    ctx.save(path)
+    c2 = R.recon_load(path)
+    a = ctx.gcd_step(4, 1.0)
+    b = R.recon_gcd_step(c2, 4, 1.0)
+    assert a == b
+    ij1, w1, s1 = ctx.get_model()
+    ij2, w2, s2 = R.recon_get_model(c2, N)
+    assert np.array_equal(ij1, ij2) and np.array_equal(w1, w2) and np.array_equal(s1, s2)
+    R.recon_destroy(c2)
