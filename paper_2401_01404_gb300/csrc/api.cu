@@ -157,7 +157,7 @@ static recon_status table_reserve(recon_ctx *c, int64_t extra) {
 static void free_ctx(recon_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void *ps[] = {c->xbits, c->xbitsT, c->phi, c->t,      c->h,      c->H,     c->xg,
+    void *ps[] = {c->xbits, c->xbitsT, c->phi, c->t,      c->h,      c->H,     c->T,     c->xg,
                   c->e,     c->mu,     c->s2,  c->Q, c->W.keys, c->W.vals, c->cnt};
     for (void *p : ps)
         if (p) cudaFree(p);
@@ -221,6 +221,7 @@ static recon_status build_state(recon_ctx *c, const void *X, int x_is_device) {
         ALLOC(c->t, rows);
         ALLOC(c->h, N * sizeof(float));
         ALLOC(c->H, N * sizeof(float));
+        ALLOC(c->T, N * sizeof(float));
         CK(launch_ising_pack((const int8_t *)Xd, M, N, (int)c->Mw, c->xbits, c->cnt, c->stream));
         CK(launch_ising_transpose_bits(c->iv(), c->xbitsT, c->stream));
         CK(ising_score_seg_setup());
@@ -823,13 +824,13 @@ extern "C" recon_status recon_get_stats(recon_ctx *c, recon_stats *out) {
 // ---------------------------------------------------------------------------
 // checkpoints
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'E', 'C', 'O', 'N', 'C', 'K', '2'};
+static const char kMagic[8] = {'R', 'E', 'C', 'O', 'N', 'C', 'K', '3'};
 
 // the tracked per-sample state, saved as is so that a resumed run continues
 // bit for bit: Ising phi, t and H; Gaussian mu and e
 static std::vector<std::pair<float *, size_t>> state_arrays(recon_ctx *c) {
     const size_t rows = (size_t)c->N * c->Mp;
-    if (c->model == RECON_ISING) return {{c->phi, rows}, {c->t, rows}, {c->H, (size_t)c->N}};
+    if (c->model == RECON_ISING) return {{c->phi, rows}, {c->t, rows}, {c->H, (size_t)c->N}, {c->T, (size_t)c->N}};
     return {{c->mu, rows}, {c->e, rows}, {c->Q, (size_t)c->N}};
 }
 
@@ -906,29 +907,42 @@ extern "C" recon_status recon_load(recon_ctx **out, const char *path, void *stre
     ok = fread(X.data(), 1, X.size(), f) == X.size() && fread(fields.data(), sizeof(float), N, f) == (size_t)N &&
          (nnz == 0 || (fread(ij.data(), sizeof(int32_t), 2 * nnz, f) == (size_t)(2 * nnz) &&
                        fread(w.data(), sizeof(float), nnz, f) == (size_t)nnz));
-    const size_t rows = (size_t)N * ((M + 31) / 32 * 32);
-    std::vector<float> s_a(rows), s_b(rows), s_c(N);
-    ok = ok && fread(s_a.data(), sizeof(float), rows, f) == rows && fread(s_b.data(), sizeof(float), rows, f) == rows &&
-         fread(s_c.data(), sizeof(float), N, f) == (size_t)N;
-    fclose(f);
-    if (!ok) return set_err(nullptr, RECON_EINVAL, "%s is truncated", path);
+    if (!ok) {
+        fclose(f);
+        return set_err(nullptr, RECON_EINVAL, "%s is truncated", path);
+    }
     // w_clamp was stored resolved; it is valid input as is
     recon_ctx *c = nullptr;
     recon_status st = recon_init(&c, X.data(), M, N, model == RECON_ISING ? RECON_X_INT8 : RECON_X_FP32, 0, model, &o,
                                  stream);
-    if (st != RECON_OK) return st;
+    if (st != RECON_OK) {
+        fclose(f);
+        return st;
+    }
     st = recon_set_model(c, ij.data(), w.data(), nnz, fields.data());
     if (st != RECON_OK) {
+        fclose(f);
         g_err = c->err;
         recon_destroy(c);
         return st;
     }
-    {
-        auto arr = state_arrays(c);
-        const float *src[3] = {s_a.data(), s_b.data(), s_c.data()};
-        for (int q = 0; q < 3; ++q)
-            CK(cudaMemcpyAsync(arr[q].first, src[q], sizeof(float) * arr[q].second, cudaMemcpyHostToDevice, c->stream));
+    // the tracked per-sample sums and per-node totals as saved, so that the run
+    // continues bit for bit (rebuilt ones could differ in their last bits)
+    for (auto &a : state_arrays(c)) {
+        std::vector<float> hbuf(a.second);
+        if (fread(hbuf.data(), sizeof(float), a.second, f) != a.second) {
+            fclose(f);
+            recon_destroy(c);
+            return set_err(nullptr, RECON_EINVAL, "%s is truncated", path);
+        }
+        if (cudaMemcpy(a.first, hbuf.data(), sizeof(float) * a.second, cudaMemcpyHostToDevice) != cudaSuccess) {
+            fclose(f);
+            g_err = "checkpoint upload failed";
+            recon_destroy(c);
+            return RECON_ECUDA;
+        }
     }
+    fclose(f);
     CK(cudaMemcpyAsync(c->cnt + CNT_NEWTON, &s.newton_passes, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->stats = s;

@@ -5,6 +5,7 @@
 //             phi    float  [N x Mp]  per-sample local field h_i + sum_j W_ij x_j
 //             t      float  [N x Mp]  tanh(phi); padding samples hold t = 1
 //             h, H   float  [N]       fields; H_i = sum_m (1 - t_i^2)
+//             T      float  [N]       sum of t_i over the Mp samples (padding t = 1)
 //   Gaussian: xg     float  [N x Mp]  samples (padding 0)
 //             e      float  [N x Mp]  residual x + s2 * mu
 //             mu     float  [N x Mp]  neighbour sums sum_j W_ij x_j
@@ -207,6 +208,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 struct IsingView {
     const uint32_t *xbits;
     float *phi, *t, *h, *H;
+    // T_i = sum of t over all Mp samples (padding included, t = 1 there), kept with H
+    // wherever t changes; the pass at delta = 0 of the pair scorer takes sum_m t_j from it
+    float *T;
     int N, M, Mp, Mw;
     // the same bits transposed per node (32 words): word l holds, at bit c, the
     // spin of sample 32 c + l (the sample lane l handles in word c)
@@ -255,7 +259,7 @@ struct recon_ctx {
     // Ising
     uint32_t *xbits = nullptr;
     uint32_t *xbitsT = nullptr;  // N x 32 words, see IsingView::xT
-    float *phi = nullptr, *t = nullptr, *h = nullptr, *H = nullptr;
+    float *phi = nullptr, *t = nullptr, *h = nullptr, *H = nullptr, *T = nullptr;
     // Gaussian
     float *xg = nullptr, *e = nullptr, *mu = nullptr, *s2 = nullptr, *Q = nullptr;
     // per-node list lengths of the first FindBest level (empty: uniform k)
@@ -292,7 +296,7 @@ struct recon_ctx {
     std::vector<cudaEvent_t> event_pool;
 
     IsingView iv() const {
-        return IsingView{xbits, phi, t, h, H, (int)N, (int)M, (int)Mp, (int)Mw, xbitsT};
+        return IsingView{xbits, phi, t, h, H, T, (int)N, (int)M, (int)Mp, (int)Mw, xbitsT};
     }
     GaussView gv() const { return GaussView{xg, e, mu, s2, Q, (int)N, (int)M, (int)Mp}; }
     bool force_exact = false;  // exact gains even in gradient-distance mode (proposal targets)

@@ -361,27 +361,25 @@ struct StageRows {
 // Pass 0 of the segmented scorer with row i staged in shared memory and both
 // rows' spins as transposed bit columns (bit c of lane l's word: sample 32 c + l):
 //   su = sum_m x_j t_i = T_i - 2 sum_{x_j = -1} t_i,
-//   sv = sum_m x_i t_j = sum_m t_j - 2 sum_{x_i = -1} t_j,
+//   sv = sum_m x_i t_j = T_j - 2 sum_{x_i = -1} t_j,
 //   dis = the samples where x_i != x_j;
-// per sample a shared-memory load or two and three adds, two of them
-// predicated on a spin bit.
+// T_i, T_j are the stored row sums, so per sample there are two adds, each
+// predicated on a spin bit, and a shared-memory load for the one over t_i.
 template <int NW>
-__device__ __forceinline__ void pass0_consume(const float *st, int lane, float Ti, uint32_t ci, const float (&t)[NW],
-                                              uint32_t cj, float &su, float &sv, int &dis) {
-    float tot0 = 0.f, tot1 = 0.f, sj0 = 0.f, sj1 = 0.f, si0 = 0.f, si1 = 0.f;
+__device__ __forceinline__ void pass0_consume(const float *st, int lane, float Ti, float Tj, uint32_t ci,
+                                              const float (&t)[NW], uint32_t cj, float &su, float &sv, int &dis) {
+    float sj0 = 0.f, sj1 = 0.f, si0 = 0.f, si1 = 0.f;
 #pragma unroll
     for (int c = 0; c < NW; c += 2) {
-        tot0 += t[c];
         if (ci & (1u << c)) sj0 += t[c];
         if (cj & (1u << c)) si0 += st[32 * c + lane];
         if (c + 1 < NW) {
-            tot1 += t[c + 1];
             if (ci & (2u << c)) sj1 += t[c + 1];
             if (cj & (2u << c)) si1 += st[32 * (c + 1) + lane];
         }
     }
     su = Ti - 2.f * warp_sum(si0 + si1);
-    sv = warp_sum((tot0 + tot1) - 2.f * (sj0 + sj1));
+    sv = Tj - 2.f * warp_sum(sj0 + sj1);
     dis = warp_sum_i(__popc(ci ^ cj));
 }
 
@@ -461,6 +459,7 @@ __global__ void k_init_fields(IsingView v, float h_clamp) {
     if (lane == 0) {
         v.h[i] = h;
         v.H[i] = hs;
+        v.T[i] = (float)v.M * th + (float)(v.Mp - v.M);
     }
 }
 
@@ -469,7 +468,7 @@ __global__ void k_phi_from_csr(IsingView v, const int64_t *off, const int32_t *n
     const int lane = threadIdx.x & 31;
     const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= v.N) return;
-    float hs = 0.f;
+    float hs = 0.f, ts = 0.f;
     const float hi = v.h[i];
     for (int m = lane; m < v.Mp; m += 32) {
         if (m >= v.M) {
@@ -487,9 +486,14 @@ __global__ void k_phi_from_csr(IsingView v, const int64_t *off, const int32_t *n
         v.phi[i * v.Mp + m] = s;
         v.t[i * v.Mp + m] = tt;
         hs += 1.f - tt * tt;
+        ts += tt;
     }
     hs = warp_sum(hs);
-    if (lane == 0) v.H[i] = hs;
+    ts = warp_sum(ts);
+    if (lane == 0) {
+        v.H[i] = hs;
+        v.T[i] = ts + (float)(v.Mp - v.M);
+    }
 }
 
 // sum over nodes and samples of x phi - log(2 cosh phi): float terms, double sums
@@ -568,7 +572,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // layout: row x (Mp floats), its bits (32 words), per warp SEG_RING stages
     // of Mp + 32 words, the stages' mbarriers, then per warp the chunk's ids,
-    // stored couplings and fields (32 each)
+    // stored couplings, fields and row sums (32 each)
     const int stw = v.Mp + 32;
     float *st = sm;
     uint32_t *sb = (uint32_t *)(sm + v.Mp);
@@ -576,28 +580,24 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
     float *myring = ring + (size_t)warp * SEG_RING * stw;
     uint64_t *bars0 = (uint64_t *)(ring + (size_t)nw * SEG_RING * stw);
     uint64_t *bars = bars0 + warp * SEG_RING;
-    int *cgj = (int *)(bars0 + nw * SEG_RING) + warp * 96;
-    float *cW0 = (float *)(cgj + 32), *cHj = (float *)(cgj + 64);
+    int *cgj = (int *)(bars0 + nw * SEG_RING) + warp * 128;
+    float *cW0 = (float *)(cgj + 32), *cHj = (float *)(cgj + 64), *cTj = (float *)(cgj + 96);
     if (lane == 0) {
         for (int r = 0; r < SEG_RING; ++r) mbar_init(bars + r, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     const int x = seg_node[sidx];
     const int gx = gid ? gid[x] : x;
-    const float *Tx = v.t + (int64_t)gx * v.Mp;
+    const float *tx = v.t + (int64_t)gx * v.Mp;
     const uint32_t *Bx = v.xbits + (int64_t)gx * v.Mw;
-    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) st[m] = Tx[m];
+    for (int m = threadIdx.x; m < v.Mp; m += blockDim.x) st[m] = tx[m];
     for (int c = threadIdx.x; c < v.Mw; c += blockDim.x) sb[c] = Bx[c];
     __syncthreads();
     const float Hx = v.H[gx];
     const int64_t start = seg_start[sidx];
     const int vbase = seg_vbase ? seg_vbase[sidx] : 0;
     unsigned long long npass = 0;
-    // sum_m t_i for pass 0 (padding samples included: st holds them)
-    float Ti = 0.f;
-#pragma unroll
-    for (int c = 0; c < NW; ++c) Ti += c < v.Mw ? st[32 * c + lane] : 0.f;
-    Ti = warp_sum(Ti);
+    const float Tx = v.T[gx];  // sum_m t_x over the Mp samples, padding included
     const uint32_t ci = __ldg(v.xT + (int64_t)gx * 32 + lane);
     const uint32_t stage_bytes = (uint32_t)(v.Mp * 4 + 128);
     const int mine = count > warp ? (count - warp + nw - 1) / nw : 0;  // candidates of this warp
@@ -622,6 +622,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
                 cgj[lane] = g;
                 cW0[lane] = wt_lookup(W, pair_key(gx, g));
                 cHj[lane] = v.H[g];
+                cTj[lane] = v.T[g];
             }
         }
         __syncwarp();
@@ -636,7 +637,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
                 ok = false;
                 break;
             }
-            const float W0 = cW0[u], Hj = cHj[u];
+            const float W0 = cW0[u], Hj = cHj[u], Tj = cTj[u];
             const float *row = myring + s * stw;
             float tj[NW];
 #pragma unroll
@@ -644,7 +645,7 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
             const uint32_t cj = ((const uint32_t *)row)[v.Mp + lane];
             float su, sv;
             int dis;
-            pass0_consume<NW>(st, lane, Ti, ci, tj, cj, su, sv, dis);
+            pass0_consume<NW>(st, lane, Tx, Tj, ci, tj, cj, su, sv, dis);
             StageRows R{st, row, ci, cj, v.Mw, lane};
             float g, w;
             int passes = 0;
@@ -734,7 +735,7 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
     const float dl = w - W0;
     if (dl != 0.f) {
         float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
-        float hi = 0.f, hj = 0.f;
+        float hi = 0.f, hj = 0.f, si_ = 0.f, sj_ = 0.f;
 #pragma unroll
         for (int c = 0; c < NWP; ++c) {
             const int m = 32 * c + lane;
@@ -751,13 +752,19 @@ __device__ __forceinline__ void update_one(IsingView v, WTable W, ScoreParams p,
                 Tj[m] = b;
                 hi += 1.f - a * a;
                 hj += 1.f - b * b;
+                si_ += a;
+                sj_ += b;
             }
         }
         hi = warp_sum(hi);
         hj = warp_sum(hj);
+        si_ = warp_sum(si_);
+        sj_ = warp_sum(sj_);
         if (lane == 0) {
             v.H[i] = hi;
             v.H[j] = hj;
+            v.T[i] = si_ + (float)(v.Mp - v.M);
+            v.T[j] = sj_ + (float)(v.Mp - v.M);
             if (!wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
         }
     }
@@ -799,7 +806,7 @@ __global__ void __launch_bounds__(256) k_update_blk(IsingView v, WTable W, Score
     const float dl = w - W0;
     if (dl != 0.f) {
         float *Ti = v.t + (int64_t)i * v.Mp, *Tj = v.t + (int64_t)j * v.Mp;
-        float hi = 0.f, hj = 0.f;
+        float hi = 0.f, hj = 0.f, si_ = 0.f, sj_ = 0.f;
 #pragma unroll
         for (int c = 0; c < NWW; ++c) {
             const int m = 32 * (R.w0 + c) + lane;
@@ -816,12 +823,17 @@ __global__ void __launch_bounds__(256) k_update_blk(IsingView v, WTable W, Score
                 Tj[m] = b;
                 hi += 1.f - a * a;
                 hj += 1.f - b * b;
+                si_ += a;
+                sj_ += b;
             }
         }
         R.sum2(hi, hj);
+        R.sum2(si_, sj_);
         if (threadIdx.x == 0) {
             v.H[i] = hi;
             v.H[j] = hj;
+            v.T[i] = si_ + (float)(v.Mp - v.M);
+            v.T[j] = sj_ + (float)(v.Mp - v.M);
             if (!wt_upsert(W, key, w)) atomicOr(&cnt[CNT_ERR], (unsigned long long)ERR_TABLE_FULL);
         }
     }
@@ -911,17 +923,20 @@ __global__ void __launch_bounds__(256) k_field(IsingView v, ScoreParams p, doubl
     if (dh != 0.f) {
         float *Pi = v.phi + i * v.Mp;
         float *Tw = v.t + i * v.Mp;
-        float hs = 0.f;
+        float hs = 0.f, ts = 0.f;
         for (int m = lane; m < v.M; m += 32) {
             float ph = Pi[m] + dh, tt = tanhf(ph);
             Pi[m] = ph;
             Tw[m] = tt;
             hs += 1.f - tt * tt;
+            ts += tt;
         }
         hs = warp_sum(hs);
+        ts = warp_sum(ts);
         if (lane == 0) {
             v.h[i] = hcur;
             v.H[i] = hs;
+            v.T[i] = ts + (float)(v.Mp - v.M);
         }
     }
     if (lane == 0) delta[i] = fabs((double)dh);
@@ -1001,7 +1016,7 @@ namespace {
 constexpr size_t SEG_SMEM_MAX = 227 * 1024;
 size_t seg_smem_bytes(int Mp, int nw) {
     return sizeof(float) * ((size_t)Mp + 32 + (size_t)nw * SEG_RING * (Mp + 32)) +
-           (size_t)nw * SEG_RING * sizeof(uint64_t) + (size_t)nw * 96 * sizeof(int);
+           (size_t)nw * SEG_RING * sizeof(uint64_t) + (size_t)nw * 128 * sizeof(int);
 }
 }  // namespace
 
