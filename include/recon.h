@@ -114,8 +114,9 @@ typedef struct {
                              general form above; by default it computes the spin product
                              X X^T in E4M3 (exact, K = M) plus a rank-two correction */
     /* A split search: with shard_count > 1 this context's screen covers only shard
-     * shard_index of its units (every shard_count-th 128 x 256 block of the pair
-     * matrix), so that shard_count processes (one GPU each) share one search.  Each
+     * shard_index of its work items (every shard_count-th 128 x 256 half of a 256 x 256
+     * super-tile of the pair matrix; with screen_pair, every shard_count-th super-tile),
+     * so that shard_count processes (one GPU each) share one search.  Each
      * returns the m best pairs of its shard (stored couplings included), and
      * recon_select_best over the union of the shards' results gives the unsharded
      * answer exactly.  Only with RECON_KNN_SCREEN (else RECON_EUNSUPPORTED);
@@ -123,6 +124,13 @@ typedef struct {
      * no sharding. */
     int32_t shard_index;
     int32_t shard_count;
+    int32_t screen_pair;  /* nonzero: the screen runs in the CTA-pair form (tcgen05
+                             cta_group::2; clusters of two CTAs, one M = 256 MMA per
+                             256 x 256 super-tile, each SM holding half of each operand
+                             tile) instead of the default one CTA per 128 x 256 unit.
+                             Both give the same survivors; the pair form moves a third
+                             less operand data but measures 5-7 % slower, its
+                             accumulator handoff crossing the two SMs. */
 } recon_options;
 
 typedef struct {

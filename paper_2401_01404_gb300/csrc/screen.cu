@@ -38,9 +38,24 @@
 // bf16 / 32 E4M3) into one of two TMEM accumulators of 256 columns, and warps
 // 0-7 drain the other accumulator (tcgen05.ld; warp w reads TMEM lanes
 // 32 (w % 4) .. + 31, one row per thread, and columns 128 (w / 4) .. + 127)
-// and stage the surviving pairs.  Every wait is bounded (1 s); on a timeout
-// the kernel sets an error word, lets its own copies land, frees TMEM and
-// returns.
+// and stage the surviving pairs.  With K = Mp (224 at M = 200) a unit's MMAs
+// take about half a microsecond, less than the round trip of either handoff
+// (a stage: MMA commit -> producer -> TMA -> MMA issuer; an accumulator: MMA
+// commit -> epilogue -> MMA issuer), and two 256-column accumulators fill the
+// TMEM: the handoffs, not the tensor pipe, set the screen's pace.  So the
+// epilogue reads each half of its columns once for a maximum, hands the
+// accumulator back at once when no row of the warp can pass (nearly always),
+// and reads the passing halves again only otherwise.  Every wait is bounded
+// (1 s); on a timeout the kernel sets an error word, lets its own copies
+// land, frees TMEM and returns.
+//
+// The CTA-pair form (recon_options.screen_pair; tcgen05 cta_group::2 in
+// clusters of two): one M = 256 MMA covers both CTAs' units of a super-tile,
+// each CTA loading its 128 rows of A and half of B (32 KB stages, six of them);
+// the commits arrive on both CTAs' barriers, the peer's tile bytes and its
+// epilogue's releases on the leader's.  It moves a third less operand data
+// per SM, but its accumulator handoff crosses the pair and it measures 5-7 %
+// slower, so the one-CTA form is the default.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -64,6 +79,19 @@ constexpr int EPI_WARPS = 8, PRODUCER_WARP = 8, MMA_WARP = 9, THREADS = 32 * (EP
 // survivors are staged per epilogue warp in shared memory and written out in
 // batches: one atomic reservation and one round of stored-coupling lookups per batch
 constexpr int SBUF = 128;
+// The CTA-pair form (tcgen05 cta_group::2, a cluster of two CTAs on the two SMs
+// of a TPC): one MMA of M = 256 covers both CTAs' 128-row units of a super-tile.
+// Each CTA holds its own 128 rows of A and one half (128 rows) of the 256 rows of
+// B per k-block, and its TMEM holds its 128 x 256 block of the product.  A stage
+// is then 32 KB instead of 48, so six stages fit where the single-CTA form has
+// four: three units of operands in flight per SM instead of two.
+template <bool PAIR>
+struct Geo {
+    static constexpr int stages = PAIR ? 6 : STAGES;
+    static constexpr int b_rows = PAIR ? BN / 2 : BN;  // rows of B held by one CTA
+    static constexpr int b_bytes = b_rows * 128;
+    static constexpr int m = PAIR ? 2 * BM : BM;       // rows of one MMA
+};
 
 // bounded wait (about 1 s of wall time); false on timeout or when another role
 // gave up.  The global timer is a slow special-register read, so it is read only
@@ -114,6 +142,87 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// --- the CTA-pair forms (every tcgen05 instruction of a kernel names one CTA group)
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+// (default semantics: the arrival only says that this warp's TMEM loads have
+// completed; a cluster-scope release would also wait for its outstanding global
+// loads, and measured a third slower)
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// the tile lands in this CTA's shared memory; its bytes count on the mbarrier at
+// a shared::cluster address (the leader CTA's)
+__device__ __forceinline__ void tma_2d_pair(void *dst, const CUtensorMap *tm, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(su32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+template <bool PAIR>
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (PAIR)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        mma_fp8(d, a, b, idesc, acc);
+}
+template <bool PAIR>
+__device__ __forceinline__ void mma_16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (PAIR)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        mma_bf16(d, a, b, idesc, acc);
+}
+// the commit's arrival reaches the mbarrier at this offset in both CTAs of the pair
+template <bool PAIR>
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    if constexpr (PAIR) {
+        const uint16_t both = 3;
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                su32(bar)),
+            "h"(both)
+            : "memory");
+    } else {
+        mma_commit(bar);
+    }
+}
+// TMEM: in the pair form one warp of each CTA takes part in the allocation
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols) {
+    if constexpr (PAIR) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+}
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t cols) {
+    if constexpr (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
 
 #define TMEM_LD32(r, taddr)                                                                                        \
     asm volatile(                                                                                                  \
@@ -229,43 +338,54 @@ struct ScreenArgs {
     unsigned long long *count;
     unsigned long long *err;
     int stall;          // fault injection: issue no loads, so the bounded waits run out
-    int shard, nshard;  // this launch covers units shard, shard + nshard, ... (a shard of the screen)
-    int64_t nlocal;     // units of this shard
+    int shard, nshard;  // this launch covers work items shard, shard + nshard, ... (a shard of the screen)
+    int64_t nlocal;     // work items of this shard: units, or in the pair form super-tiles
 };
 
-template <bool F8, bool R1>
+// PAIR: the CTA-pair form, launched in clusters of two; CTA rank r of a pair
+// works on unit 2 st + r of super-tile st (its 128 rows), rank 0 issues the MMAs
+template <bool F8, bool R1, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
                                                        const __grid_constant__ CUtensorMap tB, ScreenArgs a) {
+    using G = Geo<PAIR>;
+    constexpr int NST = G::stages;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem, *sB = smem + STAGES * A_BYTES;
-    uint64_t *full = (uint64_t *)(sB + STAGES * B_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *acc_full = empty + STAGES;   // [2]
+    uint8_t *sA = smem, *sB = smem + NST * A_BYTES;
+    uint64_t *full = (uint64_t *)(sB + NST * G::b_bytes);
+    uint64_t *empty = full + NST;
+    uint64_t *acc_full = empty + NST;      // [2]
     uint64_t *acc_empty = acc_full + 2;    // [2]
     uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     int *abort = (int *)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // the pair form: rank 0 (the leader) issues the MMAs; its full barriers count
+    // both CTAs' tile bytes and its accumulator-empty barriers both CTAs' epilogues
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const int64_t wi0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;  // first work item
+    const int64_t wstep = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
+    // the unit this CTA works on for work item t
+    auto unit_of = [&](int64_t t) -> int64_t {
+        const int64_t g = a.shard + a.nshard * t;
+        return PAIR ? 2 * g + rank : g;
+    };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full + b, 1);
-            mbar_init(acc_empty + b, EPI_WARPS);  // one arrival per epilogue warp
+            mbar_init(acc_empty + b, (PAIR ? 2 : 1) * EPI_WARPS);  // one arrival per epilogue warp
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
+    if (warp == MMA_WARP) tmem_alloc<PAIR>(tmem_slot, TMEM_COLS);
     tc_fence_before();
     __syncthreads();
+    if constexpr (PAIR) cluster_sync();  // the peer's barriers exist before anything arrives on them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -273,48 +393,68 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         if (lane == 0) {  // TMA producer
             UnitWalker walk(a.T);
             int64_t kb_all = 0;
-            for (int64_t t = blockIdx.x; t < a.nlocal && !a.stall && !*(volatile int *)abort; t += gridDim.x) {
+            for (int64_t t = wi0; t < a.nlocal && !a.stall && !*(volatile int *)abort; t += wstep) {
                 int ra, rb;
-                walk.map(a.shard + a.nshard * t, ra, rb);
+                walk.map(unit_of(t), ra, rb);
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
-                    const int s = (int)(kb_all % STAGES);
-                    if (!mbar_wait(empty + s, (uint32_t)(((kb_all / STAGES) & 1) ^ 1), abort)) break;
-                    mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-                    tma_2d(sA + s * A_BYTES, &tA, kb * (F8 ? BK8 : BK), ra, full + s);
-                    tma_2d(sB + s * B_BYTES, &tB, kb * (F8 ? BK8 : BK), rb, full + s);
+                    const int s = (int)(kb_all % NST);
+                    if (!mbar_wait(empty + s, (uint32_t)(((kb_all / NST) & 1) ^ 1), abort)) break;
+                    const int x = kb * (F8 ? BK8 : BK);
+                    if constexpr (PAIR) {
+                        // both CTAs' tiles count on the leader's full barrier
+                        if (rank == 0) mbar_expect_tx(full + s, 2 * (A_BYTES + G::b_bytes));
+                        const uint32_t fb = map_rank(full + s, 0);
+                        tma_2d_pair(sA + s * A_BYTES, &tA, x, ra, fb);
+                        tma_2d_pair(sB + s * G::b_bytes, &tB, x, rb + (int)rank * G::b_rows, fb);
+                    } else {
+                        mbar_expect_tx(full + s, A_BYTES + B_BYTES);
+                        tma_2d(sA + s * A_BYTES, &tA, x, ra, full + s);
+                        tma_2d(sB + s * B_BYTES, &tB, x, rb, full + s);
+                    }
                 }
             }
-            // let every copy issued above land before the CTA can leave
+            // let every copy issued above land before the CTA can leave (the leader's
+            // full barriers count the peer's copies too); in the pair form each CTA
+            // also waits for the MMAs' last reads of its stages (their commits arrive
+            // on its empty barriers), unless the screen gave up
             if (kb_all > 0) {
-                const int64_t first = kb_all > STAGES ? kb_all - STAGES : 0;
+                const int64_t first = kb_all > NST ? kb_all - NST : 0;
                 for (int64_t q = first; q < kb_all; ++q) {
-                    const uint64_t t0 = gtimer();
-                    while (!mbar_try(full + (q % STAGES), (uint32_t)((q / STAGES) & 1)))
-                        if (gtimer() - t0 > 1000000000ull) break;
+                    if (!PAIR || rank == 0) {
+                        const uint64_t t0 = gtimer();
+                        while (!mbar_try(full + (q % NST), (uint32_t)((q / NST) & 1)))
+                            if (gtimer() - t0 > 1000000000ull) break;
+                    }
+                    if (PAIR && !*(volatile int *)abort) {
+                        const uint64_t t0 = gtimer();
+                        while (!mbar_try(empty + (q % NST), (uint32_t)((q / NST) & 1)))
+                            if (gtimer() - t0 > 1000000000ull) break;
+                    }
                 }
             }
         }
     } else if (warp == MMA_WARP) {
-        if (lane == 0) {  // MMA issuer
-            // F32 accumulator; A and B bf16 (kind::f16: type 1) or E4M3 (kind::f8f6f4: type 0)
+        if (lane == 0 && rank == 0) {  // MMA issuer (in the pair form, the leader's only)
+            // F32 accumulator; A and B bf16 (kind::f16: type 1) or E4M3 (kind::f8f6f4: type 0);
+            // M = 256 in the pair form (128 rows per CTA), N = 256
             const uint32_t ab = F8 ? 0u : 1u;
             const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                   ((uint32_t)(BM >> 4) << 24);
+                                   ((uint32_t)(G::m >> 4) << 24);
             int64_t kb_all = 0, it = 0, last_it = -1;  // last_it: the unit of the last accumulator commit
-            for (int64_t t = blockIdx.x; t < a.nlocal && !*(volatile int *)abort; t += gridDim.x, ++it) {
+            for (int64_t t = wi0; t < a.nlocal && !*(volatile int *)abort; t += wstep, ++it) {
                 const int b = (int)(it & 1);
                 if (!mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 bool ok = true;
                 for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
-                    const int s = (int)(kb_all % STAGES);
-                    if (!mbar_wait(full + s, (uint32_t)((kb_all / STAGES) & 1), abort)) {
+                    const int s = (int)(kb_all % NST);
+                    if (!mbar_wait(full + s, (uint32_t)((kb_all / NST) & 1), abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * B_BYTES);
+                    const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * G::b_bytes);
                     // four MMAs per 128-byte k-block row (K = 16 bf16 or 32 fp8 each, 32 bytes
                     // apart: +2 in the descriptor's 16-byte address units)
                     // (straight-line issue: a data-dependent branch between the MMAs of a
@@ -325,23 +465,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                         const int nm = kb + 1 < a.nk ? 4 : a.last_mma;
                         if (nm == 4) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                            for (int k = 0; k < 4; ++k) mma_f8<PAIR>(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                         } else if (nm == 3) {
 #pragma unroll
-                            for (int k = 0; k < 3; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                            for (int k = 0; k < 3; ++k) mma_f8<PAIR>(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                         } else if (nm == 2) {
 #pragma unroll
-                            for (int k = 0; k < 2; ++k) mma_fp8(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                            for (int k = 0; k < 2; ++k) mma_f8<PAIR>(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                         } else {
-                            mma_fp8(d, da, db, idesc, kb != 0);
+                            mma_f8<PAIR>(d, da, db, idesc, kb != 0);
                         }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+                        for (int k = 0; k < 4; ++k) mma_16<PAIR>(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                     }
-                    mma_commit(empty + s);
+                    commit<PAIR>(empty + s);
                 }
-                mma_commit(acc_full + b);
+                commit<PAIR>(acc_full + b);
                 last_it = it;
                 if (!ok) break;
             }
@@ -441,13 +581,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
         int ra = 0, jt = 0;
         float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
         float2 li_n = make_float2(0.f, 0.f);
-        if ((int64_t)blockIdx.x < a.nlocal) {
-            walk.map(a.shard + a.nshard * (int64_t)blockIdx.x, ra, jt);
+        if (wi0 < a.nlocal) {
+            walk.map(unit_of(wi0), ra, jt);
             load_norms(jt, n0, n1);
             li_n = load_row(ra);
         }
         int64_t it = 0;
-        for (int64_t t = blockIdx.x; t < a.nlocal; t += gridDim.x, ++it) {
+        for (int64_t t = wi0; t < a.nlocal; t += wstep, ++it) {
             const int b = (int)(it & 1);
             const int i = ra + 32 * rg + lane;
             const int jt_cur = jt + (BN / 2) * ch;
@@ -486,8 +626,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             }
             const float ui = li, vi = li_n.y;
             // the next unit's mapping and norms, in flight during this unit's compare
-            if (t + gridDim.x < a.nlocal) {
-                walk.map(a.shard + a.nshard * (t + gridDim.x), ra, jt);
+            if (t + wstep < a.nlocal) {
+                walk.map(unit_of(t + wstep), ra, jt);
                 load_norms(jt, n0, n1);
                 li_n = load_row(ra);
             }
@@ -496,18 +636,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             if (!__all_sync(0xffffffffu, mbar_wait(acc_full + b, (uint32_t)((it >> 1) & 1), abort))) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(32 * rg) << 16) + (uint32_t)(b * BN + (BN / 2) * ch);
-            // 64 columns at a time from registers: max |g| against the unit's loosest
-            // threshold (thr - s max c_j); only a thread whose row passes that test
-            // checks its 64 columns exactly; the warp then stages its survivors
-#pragma unroll 1
+            // First pass: max |g| of each 64-column half (eight independent running
+            // maxima: one chain would serialise 64 dependent max operations) against
+            // the unit's loosest threshold thr - s max c_j.  When no row of the warp
+            // passes (the common case), the accumulator goes back to the MMA issuer at
+            // once and the next unit's MMAs run while the warp moves on; otherwise
+            // the passing halves are read again for the exact test, and the
+            // accumulator is released after it.
+            static_assert(BN == 256, "two 64-column halves per epilogue warp");
+            bool pass[BN / 128];
+#pragma unroll
             for (int hf = 0; hf < BN / 128; ++hf) {
                 uint32_t r[64];
-                const uint32_t ta = taddr + (uint32_t)(64 * hf);
-                TMEM_LD32(r, ta);
-                TMEM_LD32((r + 32), ta + 32);
+                TMEM_LD32(r, taddr + (uint32_t)(64 * hf));
+                TMEM_LD32((r + 32), taddr + (uint32_t)(64 * hf + 32));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                // eight independent running maxima (a single chain would serialise
-                // 64 dependent max operations)
                 float m8[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) m8[u] = fabsf(__uint_as_float(r[u]));
@@ -515,9 +658,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 for (int q = 8; q < 64; ++q) m8[q & 7] = fmaxf(m8[q & 7], fabsf(__uint_as_float(r[q])));
                 const float m = fmaxf(fmaxf(fmaxf(m8[0], m8[1]), fmaxf(m8[2], m8[3])),
                                       fmaxf(fmaxf(m8[4], m8[5]), fmaxf(m8[6], m8[7])));
+                pass[hf] = (R1 ? 2.f * m : m) + sc * cmax > thr_q;
+            }
+            auto release = [&]() {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if constexpr (PAIR)
+                        mbar_arrive_cluster(map_rank(acc_empty + b, 0));  // the leader's barrier
+                    else
+                        mbar_arrive(acc_empty + b);
+                }
+            };
+            bool hold = false;
+#pragma unroll
+            for (int hf = 0; hf < BN / 128; ++hf) hold |= pass[hf];
+            if (!__any_sync(0xffffffffu, hold)) {
+                release();
+                continue;
+            }
+            // the exact test of the passing halves, 64 columns at a time; the warp
+            // then stages its survivors
+#pragma unroll 1
+            for (int hf = 0; hf < BN / 128; ++hf) {
+                const bool ph = hf == 0 ? pass[0] : pass[1];
+                if (!__any_sync(0xffffffffu, ph)) continue;
+                uint32_t r[64];
+                TMEM_LD32(r, taddr + (uint32_t)(64 * hf));
+                TMEM_LD32((r + 32), taddr + (uint32_t)(64 * hf + 32));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 unsigned long long mk = 0;
                 const int j0 = jt_cur + 64 * hf;
-                if ((R1 ? 2.f * m : m) + sc * cmax > thr_q) {
+                if (ph) {
                     // exact test of the 64 columns as a bit mask (branch-free), then
                     // j > i, j < n and the stored couplings, then one reservation
                     const float4 *c4p = (const float4 *)(cn + 64 * hf);
@@ -599,17 +771,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                     nbuf += total;
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty + b);
+            release();
         }
         if (nbuf) flush();
     }
     tc_fence_before();
     __syncthreads();
+    // the pair form: neither CTA leaves (or frees TMEM) while the other's MMAs,
+    // copies or arrivals may still reach its shared memory
+    if constexpr (PAIR) cluster_sync();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        tmem_dealloc<PAIR>(tmem, TMEM_COLS);
     }
     if (threadIdx.x == 0 && *abort) atomicOr(a.err + CNT_ERR, (unsigned long long)ERR_TIMEOUT);
 }
@@ -794,6 +967,79 @@ float screen_acc_err(recon_ctx *c, bool fp8) {
     return fp8 ? (float)((2.0 * Mp / 32.0 + 1.0) / 4096.0) : (float)(2.0 * Mp * 1.2e-7);
 }
 
+namespace {
+template <bool PAIR>
+constexpr size_t screen_smem() {
+    return 1024 + (size_t)Geo<PAIR>::stages * (A_BYTES + Geo<PAIR>::b_bytes) + 256 + EPI_WARPS * BN * sizeof(float) +
+           EPI_WARPS * SBUF * sizeof(int2);
+}
+template <class Kern>
+cudaError_t set_smem(Kern k, size_t smem) {
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+// the dynamic shared-memory size of each variant, set once per device
+cudaError_t screen_set_smem(recon_ctx *c, int variant, bool pair) {
+    static int attr_device[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    int &dev = attr_device[pair ? 1 : 0][variant];
+    if (dev == c->device) return cudaSuccess;
+    cudaError_t e;
+    if (pair) {
+        const size_t sm = screen_smem<true>();
+        e = variant == 2   ? set_smem(k_screen<true, true, true>, sm)
+            : variant == 1 ? set_smem(k_screen<true, false, true>, sm)
+                           : set_smem(k_screen<false, false, true>, sm);
+    } else {
+        const size_t sm = screen_smem<false>();
+        e = variant == 2   ? set_smem(k_screen<true, true, false>, sm)
+            : variant == 1 ? set_smem(k_screen<true, false, false>, sm)
+                           : set_smem(k_screen<false, false, false>, sm);
+    }
+    if (e == cudaSuccess) dev = c->device;
+    return e;
+}
+cudaLaunchConfig_t pair_config(unsigned grid, size_t smem, cudaStream_t st, cudaLaunchAttribute *at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+template <class Kern>
+cudaError_t launch_pair(Kern k, unsigned grid, size_t smem, cudaStream_t st, const CUtensorMap &ta,
+                        const CUtensorMap &tb, const ScreenArgs &a) {
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config(grid, smem, st, at);
+    return cudaLaunchKernelEx(&cfg, k, ta, tb, a);
+}
+// clusters of two that fit on the device at once (0: the pair form cannot run),
+// per device and variant
+int screen_pair_clusters(recon_ctx *c, int variant) {
+    static int cached_dev[3] = {-1, -1, -1}, cached_n[3] = {0, 0, 0};
+    if (cached_dev[variant] == c->device) return cached_n[variant];
+    if (screen_set_smem(c, variant, true) != cudaSuccess) return 0;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config(2u * (unsigned)c->num_sms, screen_smem<true>(), c->stream, at);
+    int n = 0;
+    cudaError_t e = variant == 2   ? cudaOccupancyMaxActiveClusters(&n, k_screen<true, true, true>, &cfg)
+                    : variant == 1 ? cudaOccupancyMaxActiveClusters(&n, k_screen<true, false, true>, &cfg)
+                                   : cudaOccupancyMaxActiveClusters(&n, k_screen<false, false, true>, &cfg);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+    }
+    cached_dev[variant] = c->device;
+    cached_n[variant] = n;
+    return n;
+}
+}  // namespace
+
 cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, float thr, const float *l1,
                              float rel, int product_margin, bool skip_stored, int32_t *out, int64_t cap,
                              unsigned long long *count, double *flop_out, bool fp8, float abs_margin,
@@ -809,11 +1055,19 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
                                                          cudaEnableDefault, &q);
         if (e != cudaSuccess || !g_encode) return e != cudaSuccess ? e : cudaErrorNotSupported;
     }
+    // the pair form (on request): needs clusters of two co-resident CTAs at one per SM
+    const int variant = r1 ? 2 : fp8 ? 1 : 0;
+    bool pair = c->opt.screen_pair != 0;
+    int pair_clusters = 0;
+    if (pair) {
+        pair_clusters = screen_pair_clusters(c, variant);
+        pair = pair_clusters > 0;
+    }
     CUtensorMap ta, tb;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->N};
     const CUtensorMapDataType dt = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint64_t strides[1] = {(cuuint64_t)K * (fp8 ? 1 : 2)};
-    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, BN};
+    cuuint32_t box_a[2] = {(cuuint32_t)bke, BM}, box_b[2] = {(cuuint32_t)bke, (cuuint32_t)(pair ? BN / 2 : BN)};
     cuuint32_t es[2] = {1, 1};
     if (g_encode(&ta, dt, 2, const_cast<void *>(A), dims, strides, box_a, es,
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -822,18 +1076,8 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    const size_t smem = 1024 + STAGES * (A_BYTES + B_BYTES) + 256 + EPI_WARPS * BN * sizeof(float) +
-                        EPI_WARPS * SBUF * sizeof(int2);
-    static int attr_device[3] = {-1, -1, -1};  // per device and variant; set once for each
-    const int variant = r1 ? 2 : fp8 ? 1 : 0;
-    if (attr_device[variant] != c->device) {
-        const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        cudaError_t e = variant == 2   ? cudaFuncSetAttribute(k_screen<true, true>, at, (int)smem)
-                        : variant == 1 ? cudaFuncSetAttribute(k_screen<true, false>, at, (int)smem)
-                                       : cudaFuncSetAttribute(k_screen<false, false>, at, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_device[variant] = c->device;
-    }
+    const size_t smem = pair ? screen_smem<true>() : screen_smem<false>();
+    if (cudaError_t e = screen_set_smem(c, variant, pair); e != cudaSuccess) return e;
     ScreenArgs a;
     a.n = (int)c->N;
     a.T = (int)((c->N + SUP - 1) / SUP);
@@ -853,21 +1097,33 @@ cudaError_t launch_screen_ex(recon_ctx *c, const void *A, const void *B, int K, 
     a.count = count;
     a.err = c->cnt;
     a.stall = c->fault_screen_stall ? 1 : 0;
-    // a shard of the screen: every nshard-th unit, starting at unit `shard`
+    // a shard of the screen: every nshard-th work item (unit, or in the pair form
+    // super-tile), starting at item `shard`
+    const int64_t items = pair ? a.ntiles / 2 : a.ntiles;
     a.nshard = use_shard && c->opt.shard_count > 1 ? c->opt.shard_count : 1;
     a.shard = a.nshard > 1 ? c->opt.shard_index : 0;
-    a.nlocal = a.ntiles > a.shard ? (a.ntiles - a.shard + a.nshard - 1) / a.nshard : 0;
-    const int64_t grid = std::min<int64_t>(a.nlocal, (int64_t)c->num_sms);  // persistent: one CTA per SM
-    const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
-    if (r1)
-        k_screen<true, true><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
-    else if (fp8)
-        k_screen<true, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
-    else
-        k_screen<false, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
+    a.nlocal = items > a.shard ? (items - a.shard + a.nshard - 1) / a.nshard : 0;
+    cudaError_t e;
+    if (pair) {
+        // persistent: one cluster of two CTAs per pair of SMs
+        const unsigned g = 2u * (unsigned)std::max<int64_t>(std::min<int64_t>(a.nlocal, pair_clusters), 1);
+        e = variant == 2   ? launch_pair(k_screen<true, true, true>, g, smem, c->stream, ta, tb, a)
+            : variant == 1 ? launch_pair(k_screen<true, false, true>, g, smem, c->stream, ta, tb, a)
+                           : launch_pair(k_screen<false, false, true>, g, smem, c->stream, ta, tb, a);
+    } else {
+        const int64_t grid = std::min<int64_t>(a.nlocal, (int64_t)c->num_sms);  // persistent: one CTA per SM
+        const unsigned g = (unsigned)std::max<int64_t>(grid, 1);
+        if (r1)
+            k_screen<true, true, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
+        else if (fp8)
+            k_screen<true, false, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
+        else
+            k_screen<false, false, false><<<g, THREADS, smem, c->stream>>>(ta, tb, a);
+        e = cudaGetLastError();
+    }
     note_launch();
-    if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)a.nlocal;
-    return cudaGetLastError();
+    if (flop_out) *flop_out = 2.0 * BM * BN * (double)k_valid * (double)(pair ? 2 * a.nlocal : a.nlocal);
+    return e;
 }
 
 cudaError_t launch_screen(recon_ctx *c, const void *A, const void *B, const float *l1, int32_t *out, int64_t cap,

@@ -31,7 +31,8 @@ class recon_options(C.Structure):
                 ("knn_mode", C.c_int32), ("seed_mode", C.c_int32), ("screen_c", C.c_int32),
                 ("timing", C.c_int32), ("no_graphs", C.c_int32),
                 ("learned_frac", C.c_float), ("distance", C.c_int32), ("screen_fp8", C.c_int32),
-                ("screen_no_rank1", C.c_int32), ("shard_index", C.c_int32), ("shard_count", C.c_int32)]
+                ("screen_no_rank1", C.c_int32), ("shard_index", C.c_int32), ("shard_count", C.c_int32),
+                ("screen_pair", C.c_int32)]
 
 
 class recon_stats(C.Structure):

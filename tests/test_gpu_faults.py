@@ -60,12 +60,15 @@ def test_allocation_cap_gives_enomem(R, data):
     c.close()
 
 
-def test_stalled_screen_times_out_and_the_gpu_stays_usable(R, data):
+@pytest.mark.parametrize("pair", [0, 1])
+def test_stalled_screen_times_out_and_the_gpu_stays_usable(R, data, pair):
+    """Both screen forms: in the CTA-pair form each CTA's waits give up on their
+    own, and the pair meets at its closing cluster barrier before freeing TMEM."""
     Xs, lam = data
     ref = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN)
     p0, d0 = ref.best_pairs(16, 1.0)
     c = _with_env("RECON_FAULT_SCREEN_STALL", "1",
-                  lambda: R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN))
+                  lambda: R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_pair=pair))
     t0 = time.perf_counter()
     with pytest.raises(R.ReconError) as e:
         c.best_pairs(16, 1.0)

@@ -175,6 +175,32 @@ def test_screen_forms_agree_on_a_larger_lattice(R):
         assert pos0 == {tuple(x) for x, dv in zip(p1.tolist(), d1) if dv < 0}
 
 
+@pytest.mark.parametrize("form", ["bf16", "fp8", "rank1"])
+@pytest.mark.parametrize("N,M", [(129, 37), (300, 130), (700, 1000), (2600, 200)])
+def test_pair_form_equals_single_cta_form(R, N, M, form):
+    """The CTA-pair screen (one M = 256 MMA per super-tile over a cluster of two
+    CTAs) keeps exactly the single-CTA screen's survivors, with the same exact
+    gains: ragged last super-tiles (N not a multiple of 256), a single
+    super-tile, K from one to 32 k-blocks."""
+    X = _wl(N, M, 500 + N)
+    lam = inputs.default_lambda(N, M, 0.7)
+    Xs = np.ascontiguousarray(X.T)
+    out = []
+    for pair in (1, 0):
+        c = R.Recon(Xs, R.RECON_ISING, lam=lam, knn_mode=R.RECON_KNN_SCREEN, screen_pair=pair,
+                    timing=1, **FORMS[form])
+        kappa = (N * (N - 1) / 2 + 0.4) / N  # every survivor comes back
+        p, d = c.best_pairs(4, kappa)
+        st = c.stats()
+        assert st["screen_survivors"] == len(p) and st["screen_launches"] == 1
+        order = np.lexsort((p[:, 1], p[:, 0]))
+        out.append((p[order], d[order]))
+        c.close()
+    assert len(out[0][0]) > 0
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_fp8_screen_is_refused_for_the_gaussian_model(R):
     X = np.ones((20, 6), dtype=np.float32)
     with pytest.raises(R.ReconError) as e:
