@@ -157,6 +157,10 @@ typedef struct {
     int64_t screen_rank1;     /* screen launches in the rank-one form of the empty network */
     int64_t device_bytes;     /* device memory this context has requested since init (every
                                  allocation counted; frees are not subtracted) */
+    int64_t nnd_graph_loops;  /* NNDescent runs whose iterations went to the GPU as one graph
+                                 launch (a conditional WHILE node with the stopping test on the
+                                 device) rather than one launch and one host test per iteration
+                                 (options.timing, which times each iteration, uses the latter) */
 } recon_stats;
 
 /* Fills *opt with the defaults: lambda = 0 (set it), seed = 1,

@@ -173,6 +173,7 @@ static void free_ctx(recon_ctx *c) {
     free_search_bufs(c->sb);
     free_proposal(c->prop);
     if (c->nnd_exec) cudaGraphExecDestroy(c->nnd_exec);
+    if (c->nnd_loop_exec) cudaGraphExecDestroy(c->nnd_loop_exec);
     for (cudaEvent_t e : {c->nnd_ea, c->nnd_eb})
         if (e) cudaEventDestroy(e);
     if (c->gstream) cudaStreamDestroy(c->gstream);
@@ -300,6 +301,8 @@ extern "C" recon_status recon_init(recon_ctx **out, const void *X, int64_t M, in
     if (const char *lim = getenv("RECON_FAULT_ALLOC_LIMIT")) c->alloc_limit = strtoull(lim, nullptr, 10);
     if (const char *st = getenv("RECON_FAULT_SCREEN_STALL")) c->fault_screen_stall = atoi(st) != 0;
     if (const char *st = getenv("RECON_FAULT_SCORE_STALL")) c->fault_score_stall = atoi(st) != 0;
+    // (tests: FindBest's small-level selection and final list by the general sorts)
+    if (const char *st = getenv("RECON_FINDBEST_SORTS")) c->findbest_sorts = atoi(st) != 0;
     c->model = model;
     c->device = dev;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);

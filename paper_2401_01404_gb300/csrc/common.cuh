@@ -283,6 +283,11 @@ struct recon_ctx {
     // with (sizes, buffers, views, parameters) stays the same
     cudaGraphExec_t nnd_exec = nullptr;
     std::vector<uint8_t> nnd_sig;
+    // all of a FindBest level's NNDescent iterations as one graph: a WHILE node
+    // whose body is one iteration plus the device-side stopping test
+    cudaGraphExec_t nnd_loop_exec = nullptr;
+    std::vector<uint8_t> nnd_loop_sig;
+    bool nnd_loop_broken = false;  // the conditional graph could not be built: iterate from the host
     cudaEvent_t nnd_ea = nullptr, nnd_eb = nullptr;  // scoring launch inside the iteration (timing)
     std::string err;
     bool broken = false;
@@ -309,6 +314,7 @@ struct recon_ctx {
     // (recon_score_noalloc's static words)
     int64_t newton_extra = 0;
     bool fault_screen_stall = false, fault_score_stall = false;
+    bool findbest_sorts = false;  // FindBest without its one-CTA small-level paths
     ScoreParams sp() const {
         return ScoreParams{(float)opt.lambda, opt.w_clamp, opt.h_clamp,
                            opt.distance == RECON_DIST_GRADIENT && !force_exact ? 1 : 0, fault_score_stall ? 1 : 0};

@@ -379,6 +379,22 @@ __global__ void k_scatter_offers(const unsigned long long *Pdev, int64_t Pcap, c
 // iteration counter of a (possibly graph-replayed) NNDescent loop
 __global__ void k_next_iter(int *it) { *it += 1; }
 
+// The stopping test of Algorithm 4 on the device, at the end of an iteration of
+// the graph's WHILE loop: go on while more than eps of the list entries changed
+// (k_merge's count), fewer than max_iters iterations ran and no error was
+// raised.  Also adds up what the host loop reads after each iteration:
+// acc[0] candidates scored, acc[1] offers dropped for want of space.
+__global__ void k_nnd_continue(cudaGraphConditionalHandle h, const unsigned long long *cnt, const int *iter,
+                               int max_iters, double klen_sum, double eps, unsigned long long cand_cap,
+                               unsigned long long *acc) {
+    const unsigned long long ncand = cnt[CNT_SCRATCH0] < cand_cap ? cnt[CNT_SCRATCH0] : cand_cap;
+    acc[0] += ncand;
+    acc[1] += cnt[CNT_SCRATCH3];
+    const bool converged = (double)cnt[CNT_SCRATCH2] / klen_sum < eps;
+    const bool go = !converged && *iter < max_iters && cnt[CNT_ERR] == 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // best k of (old list u offers) per node; old entries win ties.  A warp holds
 // the list, entry r in lane r (slot A) and entry r + 32 in lane r (slot B), so
 // lists of up to 64 entries; node x keeps klen[x] of them.
@@ -490,6 +506,174 @@ __global__ void k_take_D(int64_t nDp, int k, const int32_t *gid, const int32_t *
     Dp[2 * pos] = a < b ? a : b;
     Dp[2 * pos + 1] = a < b ? b : a;
     Dd[pos] = dd[e];
+}
+
+// D+ of a small level (n k <= SEL_SMALL keys) in one CTA of 1024 threads,
+// instead of a full sort: the want-th smallest key T, digit by digit from the
+// top (eight 8-bit histogram passes over keys that sit in L2 at this size),
+// then every key below T and the lowest-index ones of the keys equal to T,
+// which are the first `want` keys of a stable sort.  Writes their edge
+// indices to out_e[0 .. want), in no particular order (D is a set).
+constexpr int64_t SEL_SMALL = 1 << 16;
+__global__ void __launch_bounds__(1024) k_select_small(int64_t nk, int64_t want, const unsigned long long *keys,
+                                                       uint32_t *out_e) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t wcount[32];
+    __shared__ unsigned long long s_prefix, s_out;
+    __shared__ long long s_rem, s_eq;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) {
+        s_prefix = 0;
+        s_rem = want;
+        s_out = 0;
+        s_eq = 0;
+    }
+    unsigned long long mask = 0;
+    __syncthreads();
+    for (int pass = 7; pass >= 0; --pass) {
+        if (tid < 256) hist[tid] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix;
+        const int sh = 8 * pass;
+        for (int64_t e = tid; e < nk; e += blockDim.x) {
+            const unsigned long long k = keys[e];
+            if ((k & mask) == prefix) atomicAdd(&hist[(uint32_t)(k >> sh) & 255u], 1u);
+        }
+        __syncthreads();
+        if (w == 0) {  // the bucket that holds the rem-th key of the prefix: lane l scans buckets 8l .. 8l + 7
+            uint32_t c8[8], sum = 0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c8[u] = hist[8 * lane + u];
+                sum += c8[u];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const long long rem = s_rem;
+            long long acc = (long long)(incl - sum);
+            if (acc < rem && rem <= (long long)incl) {
+                int bk = 8 * lane + 7;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (acc + (long long)c8[u] >= rem) {
+                        bk = 8 * lane + u;
+                        break;
+                    }
+                    acc += c8[u];
+                }
+                s_rem = rem - acc;
+                s_prefix = prefix | ((unsigned long long)bk << sh);
+            }
+        }
+        mask |= 255ull << sh;
+        __syncthreads();
+    }
+    const unsigned long long T = s_prefix;
+    const long long take_eq = s_rem;  // keys equal to T still to take, lowest indices first
+    for (int64_t e0 = 0; e0 < nk; e0 += blockDim.x) {
+        const int64_t e = e0 + tid;
+        const unsigned long long k = e < nk ? keys[e] : ~0ull;
+        const bool eq = e < nk && k == T;
+        const uint32_t be = __ballot_sync(0xffffffffu, eq);
+        if (lane == 0) wcount[w] = (uint32_t)__popc(be);
+        __syncthreads();
+        long long before = s_eq + __popc(be & ((1u << lane) - 1u));
+        for (int u = 0; u < w; ++u) before += wcount[u];
+        const bool take = (e < nk && k < T) || (eq && before < take_eq);
+        const uint32_t bt = __ballot_sync(0xffffffffu, take);
+        unsigned long long base = 0;
+        if (lane == 0 && bt) base = atomicAdd(&s_out, (unsigned long long)__popc(bt));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (take) out_e[base + __popc(bt & ((1u << lane) - 1u))] = (uint32_t)e;
+        __syncthreads();
+        if (tid == 0) {
+            long long tot = 0;
+            for (int u = 0; u < 32; ++u) tot += wcount[u];
+            s_eq += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// The final list of a small result set (P <= FIN_SMALL pairs) in one CTA: a
+// bitonic sort in shared memory by (d, i, j, position) -- the order that the
+// stable radix sorts give -- then the first of each run of equal pairs, the
+// m best of them to outp/outd and their number to *count.
+constexpr int64_t FIN_SMALL = 8192;
+struct FinItem {
+    uint32_t dk;  // float_key(d)
+    int32_t i, j;
+    uint32_t q;   // position in the input
+};
+__device__ __forceinline__ bool fin_less(const FinItem &a, const FinItem &b) {
+    if (a.dk != b.dk) return a.dk < b.dk;
+    if (a.i != b.i) return a.i < b.i;
+    if (a.j != b.j) return a.j < b.j;
+    return a.q < b.q;
+}
+__global__ void __launch_bounds__(1024) k_finish_small(int P, int np2, int64_t m, const int32_t *pairs, const float *dd,
+                                                       int32_t *outp, float *outd, unsigned long long *count) {
+    extern __shared__ __align__(16) FinItem it[];
+    __shared__ uint32_t wcount[32];
+    __shared__ long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int q = tid; q < np2; q += blockDim.x) {
+        FinItem x;
+        if (q < P) {
+            x.dk = float_key(dd[q]);
+            x.i = pairs[2 * q];
+            x.j = pairs[2 * q + 1];
+            x.q = (uint32_t)q;
+        } else {  // after every real entry
+            x.dk = 0xffffffffu;
+            x.i = 0x7fffffff;
+            x.j = 0x7fffffff;
+            x.q = 0xffffffffu;
+        }
+        it[q] = x;
+    }
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (int size = 2; size <= np2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < np2 / 2; t += blockDim.x) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const FinItem a = it[lo], b = it[hi];
+                if (up ? fin_less(b, a) : fin_less(a, b)) {
+                    it[lo] = b;
+                    it[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int q0 = 0; q0 < P; q0 += blockDim.x) {
+        const int q = q0 + tid;
+        const bool first = q < P && (q == 0 || it[q].i != it[q - 1].i || it[q].j != it[q - 1].j);
+        const uint32_t bf = __ballot_sync(0xffffffffu, first);
+        if (lane == 0) wcount[w] = (uint32_t)__popc(bf);
+        __syncthreads();
+        long long pos = s_base + __popc(bf & ((1u << lane) - 1u));
+        for (int u = 0; u < w; ++u) pos += wcount[u];
+        if (first && pos < m) {
+            const FinItem x = it[q];
+            outp[2 * pos] = x.i;
+            outp[2 * pos + 1] = x.j;
+            outd[pos] = dd[x.q];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            long long tot = 0;
+            for (int u = 0; u < 32; ++u) tot += wcount[u];
+            s_base += tot;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *count = (unsigned long long)(s_base < m ? s_base : m);
 }
 
 // saturated nodes: every out-edge in D
@@ -1143,7 +1327,9 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
     // the candidate, offer and change counts and the error word.
     // timing events inside a capture become record nodes of the graph
     unsigned rec_flags = cudaEventRecordDefault;
-    auto enqueue = [&]() -> cudaError_t {
+    // one iteration; readback: its counts to the host, for the host loop's
+    // stopping test (the device loop tests on the device)
+    auto enqueue = [&](bool readback) -> cudaError_t {
         cudaError_t e;
         k_next_iter<<<1, 1, 0, gs>>>((int *)S.iter.p);
         note_launch();
@@ -1212,6 +1398,7 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
                                                               (int64_t *)S.inoff.p, (int32_t *)S.off_sv.p,
                                                               (float *)S.off_sd.p, counter(c, CNT_SCRATCH2));
         note_launch();
+        if (!readback) return cudaGetLastError();
         // counts back to the host: candidates, offers, changes, drops; and the error word
         if ((e = cudaMemcpyAsync(c->cnt_host + CNT_SCRATCH0, c->cnt + CNT_SCRATCH0, sizeof(unsigned long long) * 4,
                                  cudaMemcpyDeviceToHost, gs)))
@@ -1249,9 +1436,100 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
             put(&v, sizeof v);
         }
     }
+    int it = 0;
+    recon_status result = RECON_OK;
+    bool done = false;  // the device loop ran the iterations
+    // Without per-iteration timing, every iteration goes into one graph launch: a
+    // WHILE node whose body is an iteration followed by k_nnd_continue, the
+    // stopping test on the device.  One launch and one synchronisation per
+    // level instead of one of each per iteration; when the conditional graph
+    // cannot be built, the host loop below runs instead.
+    if (use_graph && !ea && !c->nnd_loop_broken) {
+        GROW(S.nnd_acc, sizeof(unsigned long long) * 2);
+        std::vector<uint8_t> lsig = sig;
+        {
+            const double lp[] = {(double)max_iters, (double)S.klen_sum, c->opt.eps_knn,
+                                 (double)(uintptr_t)S.nnd_acc.p};
+            const uint8_t *b = (const uint8_t *)lp;
+            lsig.insert(lsig.end(), b, b + sizeof lp);
+        }
+        if (c->nnd_loop_exec && lsig != c->nnd_loop_sig) {
+            cudaGraphExecDestroy(c->nnd_loop_exec);
+            c->nnd_loop_exec = nullptr;
+            c->nnd_loop_sig.clear();
+        }
+        if (!c->nnd_loop_exec) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaGraphCreate(&g, 0);
+            cudaGraphConditionalHandle h{};
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+            if (e == cudaSuccess) {
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(gs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const int64_t l0 = c->stats.kernel_launches;
+                    cudaError_t ce = enqueue(false);
+                    if (ce == cudaSuccess) {
+                        k_nnd_continue<<<1, 1, 0, gs>>>(h, c->cnt, (const int *)S.iter.p, max_iters,
+                                                        (double)S.klen_sum, c->opt.eps_knn,
+                                                        (unsigned long long)cand_cap,
+                                                        (unsigned long long *)S.nnd_acc.p);
+                        note_launch();
+                        ce = cudaGetLastError();
+                    }
+                    c->graph_launches_per_iter = c->stats.kernel_launches - l0;
+                    c->stats.kernel_launches = l0;
+                    cudaGraph_t out = nullptr;
+                    const cudaError_t ee = cudaStreamEndCapture(gs, &out);
+                    e = ce != cudaSuccess ? ce : ee;
+                }
+            }
+            cudaGraphExec_t ex = nullptr;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) {
+                c->nnd_loop_exec = ex;
+                c->nnd_loop_sig = std::move(lsig);
+            } else {
+                (void)cudaGetLastError();
+                c->nnd_loop_broken = true;
+            }
+        }
+        if (c->nnd_loop_exec) {
+            unsigned long long acc_h[2] = {0, 0};
+            int iters_h = 0;
+            cudaError_t e = cudaMemsetAsync(S.nnd_acc.p, 0, sizeof(unsigned long long) * 2, gs);
+            if (e == cudaSuccess) e = cudaGraphLaunch(c->nnd_loop_exec, gs);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(acc_h, S.nnd_acc.p, sizeof acc_h, cudaMemcpyDeviceToHost, gs);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&iters_h, S.iter.p, sizeof(int), cudaMemcpyDeviceToHost, gs);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->cnt_host + CNT_ERR, c->cnt + CNT_ERR, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, gs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+            if (e != cudaSuccess) {
+                result = cuda_fail(c, e, "NNDescent iterations");
+            } else {
+                it = iters_h;
+                c->stats.kernel_launches += c->graph_launches_per_iter * (int64_t)it;
+                c->stats.pair_evals += (int64_t)acc_h[0];
+                c->stats.dropped_offers += (int64_t)acc_h[1];
+                c->stats.nnd_graph_loops += 1;
+                if (c->cnt_host[CNT_ERR]) result = check_err_flags(c, "NNDescent");
+            }
+            done = true;
+        }
+    }
     cudaGraphExec_t exec = nullptr;
-    if (use_graph && c->nnd_exec && sig == c->nnd_sig) exec = c->nnd_exec;
-    if (use_graph && !exec) {
+    if (!done && use_graph && c->nnd_exec && sig == c->nnd_sig) exec = c->nnd_exec;
+    if (!done && use_graph && !exec) {
         if (c->nnd_exec) {
             cudaGraphExecDestroy(c->nnd_exec);
             c->nnd_exec = nullptr;
@@ -1263,7 +1541,7 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
         cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             rec_flags = cudaEventRecordExternal;
-            cudaError_t ce = enqueue();
+            cudaError_t ce = enqueue(true);
             rec_flags = cudaEventRecordDefault;
             cudaError_t ee = cudaStreamEndCapture(gs, &graph);
             e = ce != cudaSuccess ? ce : ee;
@@ -1280,16 +1558,14 @@ static recon_status knn_nndescent(recon_ctx *c, const int32_t *gid, int n, int k
             c->nnd_sig = std::move(sig);
         }
     }
-    int it = 0;
-    recon_status result = RECON_OK;
-    for (it = 0; it < max_iters;) {
+    while (!done && it < max_iters) {
         ++it;
         cudaError_t e;
         if (exec) {
             e = cudaGraphLaunch(exec, gs);
             c->stats.kernel_launches += c->graph_launches_per_iter;
         } else
-            e = enqueue();
+            e = enqueue(true);
         if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
         if (e != cudaSuccess) {
             result = cuda_fail(c, e, "NNDescent iteration");
@@ -1337,6 +1613,26 @@ static recon_status finish_results(recon_ctx *c, int64_t m, int64_t *count) {
     GROW(S.scan_tmp2, sizeof(int64_t) * scan_tmp_elems(P));
     GROW(S.out_pairs, sizeof(int32_t) * 2 * std::max<int64_t>(m, 1));
     GROW(S.out_d, sizeof(float) * std::max<int64_t>(m, 1));
+    if (P <= FIN_SMALL && !c->findbest_sorts) {  // one CTA: sort in shared memory, unique, gather
+        int np2 = 1;
+        while (np2 < P) np2 <<= 1;
+        const size_t smem = sizeof(FinItem) * (size_t)np2;
+        static int attr_device = -1;
+        if (attr_device != c->device) {
+            CKS(cudaFuncSetAttribute(k_finish_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(FinItem) * FIN_SMALL)));
+            attr_device = c->device;
+        }
+        k_finish_small<<<1, 1024, smem, c->stream>>>((int)P, np2, m, (int32_t *)S.res_pairs.p, (float *)S.res_d.p,
+                                                      (int32_t *)S.out_pairs.p, (float *)S.out_d.p,
+                                                      counter(c, CNT_SCRATCH2)); note_launch();
+        CKS(cudaGetLastError());
+        unsigned long long nout = 0;
+        recon_status st = read_counter(c, CNT_SCRATCH2, &nout);
+        if (st != RECON_OK) return st;
+        *count = (int64_t)nout;
+        return RECON_OK;
+    }
     k_pair_keys<<<nblk(P), 256, 0, c->stream>>>(P, (int32_t *)S.res_pairs.p, (unsigned long long *)S.fk.p,
                                                 (uint32_t *)S.fv.p); note_launch();
     CKS(cudaGetLastError());
@@ -1471,9 +1767,17 @@ recon_status findbest_run(recon_ctx *c, int k_cfg, int64_t m, int32_t **pairs_de
         k_edge_keys<<<nblk(nk), 256, 0, c->stream>>>((int)n, k, gid, (int32_t *)S.knn_id.p, (float *)S.knn_d.p,
                                                      (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p); note_launch();
         CKS(cudaGetLastError());
-        st = sort_kv(c, (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p, nk, 0, 64);
-        if (st != RECON_OK) return st;
         const int64_t nDp = std::min<int64_t>(2 * m, S.klen_sum);
+        if (nk <= SEL_SMALL && !c->findbest_sorts) {  // one CTA selects the nDp best keys (a set: D+ needs no order)
+            if (nDp > 0) {
+                k_select_small<<<1, 1024, 0, c->stream>>>(nk, nDp, (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p);
+                note_launch();
+                CKS(cudaGetLastError());
+            }
+        } else {
+            st = sort_kv(c, (unsigned long long *)S.ek.p, (uint32_t *)S.ev.p, nk, 0, 64);
+            if (st != RECON_OK) return st;
+        }
         // D : unique pairs of D+
         uint64_t dcap = 1;
         while (dcap < (uint64_t)(4 * nDp + 64)) dcap <<= 1;

@@ -29,6 +29,7 @@ struct SearchBufs {
     DBuf iter;                                    // device-side iteration counter
     DBuf g0_id, g0_d, g0_klen;                    // first-level lists, kept when a later level runs
     DBuf seed;                                    // device copy of the search's seed
+    DBuf nnd_acc;                                 // the device loop's sums: candidates, dropped offers
     int64_t res_n = 0;
     int64_t klen_sum = 0;
     // the k-NN graph of the first level: rows g0_n, stride g0_K (0: no lists);
@@ -42,7 +43,7 @@ struct SearchBufs {
                 &scan_in, &scan_tmp, &scan_tmp2, &cand, &cand_d, &seg_node, &seg_start, &seg_count, &seg_vbase, &off_t, &off_v, &off_d, &off_sv,
                 &off_sd, &pairs_tmp, &ek, &ev, &dset, &flag, &pos, &gid_a, &gid_b, &ex_pairs, &ex_d,
                 &ex_keys, &ex_vals, &dense, &res_pairs, &res_d, &fk, &fv, &fk2, &fv2, &out_pairs,
-                &out_d, &sort_k2, &sort_v2, &sort_tmp, &scr_A, &scr_B, &scr_l1, &klen, &iter, &g0_id, &g0_d, &g0_klen, &seed};
+                &out_d, &sort_k2, &sort_v2, &sort_tmp, &scr_A, &scr_B, &scr_l1, &klen, &iter, &g0_id, &g0_d, &g0_klen, &seed, &nnd_acc};
     }
 };
 

@@ -43,7 +43,7 @@ class recon_stats(C.Structure):
                 ("screen_launches", C.c_int64), ("screen_ms", C.c_double), ("screen_flop", C.c_double),
                 ("screen_survivors", C.c_int64), ("seeded_nodes", C.c_int64), ("tuned_threads", C.c_int64),
                 ("dropped_offers", C.c_int64), ("screen_rank1", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("nnd_graph_loops", C.c_int64)]
 
 
 class recon_peaks(C.Structure):
@@ -294,7 +294,8 @@ def recon_get_stats(ctx) -> dict:
             "score_pairs": s.score_pairs, "score_ms": s.score_ms, "screen_launches": s.screen_launches,
             "screen_ms": s.screen_ms, "screen_flop": s.screen_flop, "screen_survivors": s.screen_survivors,
             "seeded_nodes": s.seeded_nodes, "tuned_threads": s.tuned_threads,
-            "dropped_offers": s.dropped_offers, "screen_rank1": s.screen_rank1, "device_bytes": s.device_bytes}
+            "dropped_offers": s.dropped_offers, "screen_rank1": s.screen_rank1, "device_bytes": s.device_bytes,
+            "nnd_graph_loops": s.nnd_graph_loops}
 
 
 def recon_set_list_lengths(ctx, k=None):
