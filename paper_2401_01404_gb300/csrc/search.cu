@@ -513,20 +513,29 @@ __global__ void k_take_D(int64_t nDp, int k, const int32_t *gid, const int32_t *
 // top (eight 8-bit histogram passes over keys that sit in L2 at this size),
 // then every key below T and the lowest-index ones of the keys equal to T,
 // which are the first `want` keys of a stable sort.  Writes their edge
-// indices to out_e[0 .. want), in no particular order (D is a set).
+// indices to out_e[0 .. want), in no particular order (D is a set).  Each
+// thread keeps SEL_BATCH loads in flight; a key equals T only for the two
+// directed copies of one pair (the key holds d and a hash of the pair), so the
+// equal keys go to a small buffer and are ordered by index at the end (more
+// than SEL_EQ of them, and the compaction runs again in index order).
 constexpr int64_t SEL_SMALL = 1 << 16;
+constexpr int SEL_BATCH = 8, SEL_EQ = 256;
 __global__ void __launch_bounds__(1024) k_select_small(int64_t nk, int64_t want, const unsigned long long *keys,
                                                        uint32_t *out_e) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t wcount[32];
+    __shared__ uint32_t eqbuf[SEL_EQ];
     __shared__ unsigned long long s_prefix, s_out;
     __shared__ long long s_rem, s_eq;
+    __shared__ uint32_t s_neq;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    constexpr int NT = 1024;
     if (tid == 0) {
         s_prefix = 0;
         s_rem = want;
         s_out = 0;
         s_eq = 0;
+        s_neq = 0;
     }
     unsigned long long mask = 0;
     __syncthreads();
@@ -535,9 +544,25 @@ __global__ void __launch_bounds__(1024) k_select_small(int64_t nk, int64_t want,
         __syncthreads();
         const unsigned long long prefix = s_prefix;
         const int sh = 8 * pass;
-        for (int64_t e = tid; e < nk; e += blockDim.x) {
-            const unsigned long long k = keys[e];
-            if ((k & mask) == prefix) atomicAdd(&hist[(uint32_t)(k >> sh) & 255u], 1u);
+        for (int64_t e0 = 0; e0 < nk; e0 += (int64_t)NT * SEL_BATCH) {
+            unsigned long long kk[SEL_BATCH];
+#pragma unroll
+            for (int u = 0; u < SEL_BATCH; ++u) {
+                const int64_t e = e0 + (int64_t)u * NT + tid;
+                kk[u] = e < nk ? keys[e] : ~0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < SEL_BATCH; ++u) {
+                const int64_t e = e0 + (int64_t)u * NT + tid;
+                const uint32_t dg = (e < nk && (kk[u] & mask) == prefix) ? (uint32_t)(kk[u] >> sh) & 255u : 256u;
+                // the common case in the leading bytes: the whole warp holds one digit
+                const uint32_t d0 = __shfl_sync(0xffffffffu, dg, 0);
+                if (__all_sync(0xffffffffu, dg == d0)) {
+                    if (lane == 0 && d0 < 256u) atomicAdd(&hist[d0], 32u);
+                } else if (dg < 256u) {
+                    atomicAdd(&hist[dg], 1u);
+                }
+            }
         }
         __syncthreads();
         if (w == 0) {  // the bucket that holds the rem-th key of the prefix: lane l scans buckets 8l .. 8l + 7
@@ -573,22 +598,52 @@ __global__ void __launch_bounds__(1024) k_select_small(int64_t nk, int64_t want,
         __syncthreads();
     }
     const unsigned long long T = s_prefix;
-    const long long take_eq = s_rem;  // keys equal to T still to take, lowest indices first
-    for (int64_t e0 = 0; e0 < nk; e0 += blockDim.x) {
+    const long long take_eq = s_rem;  // keys equal to T to take, lowest indices first
+    // one pass: keys below T straight to the output, keys equal to T to the buffer
+    for (int64_t e0 = 0; e0 < nk; e0 += (int64_t)NT * SEL_BATCH) {
+        unsigned long long kk[SEL_BATCH];
+#pragma unroll
+        for (int u = 0; u < SEL_BATCH; ++u) {
+            const int64_t e = e0 + (int64_t)u * NT + tid;
+            kk[u] = e < nk ? keys[e] : ~0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < SEL_BATCH; ++u) {
+            const int64_t e = e0 + (int64_t)u * NT + tid;
+            const bool lt = e < nk && kk[u] < T;
+            const uint32_t bt = __ballot_sync(0xffffffffu, lt);
+            unsigned long long base = 0;
+            if (lane == 0 && bt) base = atomicAdd(&s_out, (unsigned long long)__popc(bt));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (lt) out_e[base + __popc(bt & ((1u << lane) - 1u))] = (uint32_t)e;
+            if (e < nk && kk[u] == T) {
+                const uint32_t q = atomicAdd(&s_neq, 1u);
+                if (q < SEL_EQ) eqbuf[q] = (uint32_t)e;
+            }
+        }
+    }
+    __syncthreads();
+    const uint32_t neq = s_neq;
+    if (neq <= (uint32_t)SEL_EQ) {
+        // the take_eq lowest indices of the buffer (at most SEL_EQ entries): rank by count
+        for (uint32_t q = tid; q < neq; q += NT) {
+            const uint32_t e = eqbuf[q];
+            uint32_t r = 0;
+            for (uint32_t o = 0; o < neq; ++o) r += eqbuf[o] < e;
+            if ((long long)r < take_eq) out_e[(want - take_eq) + r] = e;
+        }
+        return;
+    }
+    // many equal keys (hash collisions at the cut): their lowest indices in index order
+    for (int64_t e0 = 0; e0 < nk; e0 += NT) {
         const int64_t e = e0 + tid;
-        const unsigned long long k = e < nk ? keys[e] : ~0ull;
-        const bool eq = e < nk && k == T;
+        const bool eq = e < nk && keys[e] == T;
         const uint32_t be = __ballot_sync(0xffffffffu, eq);
         if (lane == 0) wcount[w] = (uint32_t)__popc(be);
         __syncthreads();
         long long before = s_eq + __popc(be & ((1u << lane) - 1u));
         for (int u = 0; u < w; ++u) before += wcount[u];
-        const bool take = (e < nk && k < T) || (eq && before < take_eq);
-        const uint32_t bt = __ballot_sync(0xffffffffu, take);
-        unsigned long long base = 0;
-        if (lane == 0 && bt) base = atomicAdd(&s_out, (unsigned long long)__popc(bt));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take) out_e[base + __popc(bt & ((1u << lane) - 1u))] = (uint32_t)e;
+        if (eq && before < take_eq) out_e[(want - take_eq) + before] = (uint32_t)e;
         __syncthreads();
         if (tid == 0) {
             long long tot = 0;
