@@ -348,11 +348,18 @@ template <bool F8, bool R1, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ CUtensorMap tA,
                                                        const __grid_constant__ CUtensorMap tB, ScreenArgs a) {
     using G = Geo<PAIR>;
-    constexpr int NST = G::stages;
+    // k-blocks per stage: the rank-one form (K = Mp, two k-blocks at M = 200) keeps a
+    // unit's k-blocks in one stage, so that its MMA thread polls one full barrier and
+    // commits one empty barrier per unit instead of one per k-block; at K = 224 that
+    // thread's polls and commits take as long as the tensor pipe's work.  The same
+    // bytes in flight: two stages of two k-blocks instead of four of one.
+    constexpr int KPS = (R1 && !PAIR) ? 2 : 1;
+    constexpr int NST = G::stages / KPS;
+    static_assert(NST * KPS == G::stages, "stages hold whole k-block groups");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem, *sB = smem + NST * A_BYTES;
-    uint64_t *full = (uint64_t *)(sB + NST * G::b_bytes);
+    uint8_t *sA = smem, *sB = smem + NST * KPS * A_BYTES;
+    uint64_t *full = (uint64_t *)(sB + NST * KPS * G::b_bytes);
     uint64_t *empty = full + NST;
     uint64_t *acc_full = empty + NST;      // [2]
     uint64_t *acc_empty = acc_full + 2;    // [2]
@@ -392,15 +399,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     if (warp == PRODUCER_WARP) {
         if (lane == 0) {  // TMA producer
             UnitWalker walk(a.T);
-            int64_t kb_all = 0;
+            int64_t kb_all = 0;  // stages filled so far
             for (int64_t t = wi0; t < a.nlocal && !a.stall && !*(volatile int *)abort; t += wstep) {
                 int ra, rb;
                 walk.map(unit_of(t), ra, rb);
-                for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
+                for (int kb = 0; kb < a.nk; kb += KPS, ++kb_all) {
                     const int s = (int)(kb_all % NST);
                     if (!mbar_wait(empty + s, (uint32_t)(((kb_all / NST) & 1) ^ 1), abort)) break;
                     const int x = kb * (F8 ? BK8 : BK);
-                    if constexpr (PAIR) {
+                    if constexpr (KPS > 1) {
+                        const int nkb = min(KPS, a.nk - kb);
+                        mbar_expect_tx(full + s, (uint32_t)nkb * (A_BYTES + B_BYTES));
+                        for (int j = 0; j < nkb; ++j) {
+                            const int xj = (kb + j) * (F8 ? BK8 : BK);
+                            tma_2d(sA + (s * KPS + j) * A_BYTES, &tA, xj, ra, full + s);
+                            tma_2d(sB + (s * KPS + j) * B_BYTES, &tB, xj, rb, full + s);
+                        }
+                    } else if constexpr (PAIR) {
                         // both CTAs' tiles count on the leader's full barrier
                         if (rank == 0) mbar_expect_tx(full + s, 2 * (A_BYTES + G::b_bytes));
                         const uint32_t fb = map_rank(full + s, 0);
@@ -447,14 +462,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 bool ok = true;
-                for (int kb = 0; kb < a.nk; ++kb, ++kb_all) {
+                for (int kb0 = 0; kb0 < a.nk; kb0 += KPS, ++kb_all) {
                     const int s = (int)(kb_all % NST);
                     if (!mbar_wait(full + s, (uint32_t)((kb_all / NST) & 1), abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t da = desc_sw128(sA + s * A_BYTES), db = desc_sw128(sB + s * G::b_bytes);
+#pragma unroll
+                    for (int j = 0; j < KPS; ++j) {
+                    const int kb = kb0 + j;
+                    if (KPS > 1 && kb >= a.nk) break;
+                    const uint64_t da = desc_sw128(sA + (s * KPS + j) * A_BYTES),
+                                   db = desc_sw128(sB + (s * KPS + j) * G::b_bytes);
                     // four MMAs per 128-byte k-block row (K = 16 bf16 or 32 fp8 each, 32 bytes
                     // apart: +2 in the descriptor's 16-byte address units)
                     // (straight-line issue: a data-dependent branch between the MMAs of a
@@ -479,6 +499,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
 #pragma unroll
                         for (int k = 0; k < 4; ++k) mma_16<PAIR>(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
                     }
+                    }  // k-blocks of the stage
                     commit<PAIR>(empty + s);
                 }
                 commit<PAIR>(acc_full + b);
