@@ -370,6 +370,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     // the pair form: rank 0 (the leader) issues the MMAs; its full barriers count
     // both CTAs' tile bytes and its accumulator-empty barriers both CTAs' epilogues
     const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    // One stage per unit (the rank-one form with K <= 2 k-blocks): the producer also
+    // waits for the unit's accumulator to be free and then adds a second arrival to
+    // the stage's full barrier, so the MMA thread polls one barrier per unit (each
+    // poll costs that thread about 80 ns, and its polls, MMA issues and commits are
+    // what bound the screen at K = 224).
+    const bool unit_stage = KPS > 1 && a.nk <= KPS;
     const int64_t wi0 = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;  // first work item
     const int64_t wstep = PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
     // the unit this CTA works on for work item t
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
-            mbar_init(full + s, 1);
+            mbar_init(full + s, unit_stage ? 2 : 1);
             mbar_init(empty + s, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -414,6 +420,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
                             const int xj = (kb + j) * (F8 ? BK8 : BK);
                             tma_2d(sA + (s * KPS + j) * A_BYTES, &tA, xj, ra, full + s);
                             tma_2d(sB + (s * KPS + j) * B_BYTES, &tB, xj, rb, full + s);
+                        }
+                        if (unit_stage) {  // unit kb_all's accumulator, then the second arrival
+                            if (!mbar_wait(acc_empty + (kb_all & 1), (uint32_t)(((kb_all >> 1) & 1) ^ 1), abort))
+                                break;
+                            mbar_arrive(full + s);
                         }
                     } else if constexpr (PAIR) {
                         // both CTAs' tiles count on the leader's full barrier
@@ -458,7 +469,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_screen(const __grid_constant__ C
             int64_t kb_all = 0, it = 0, last_it = -1;  // last_it: the unit of the last accumulator commit
             for (int64_t t = wi0; t < a.nlocal && !*(volatile int *)abort; t += wstep, ++it) {
                 const int b = (int)(it & 1);
-                if (!mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
+                // (one stage per unit: the stage's full barrier already includes this)
+                if (!unit_stage && !mbar_wait(acc_empty + b, (uint32_t)(((it >> 1) & 1) ^ 1), abort)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 bool ok = true;
