@@ -279,7 +279,9 @@ def _c2_leg(R, stream, peaks, steps, workload="ising_n2000_m1000", recall=True):
         l2 = peaks.get("l2_read_gbs")
         fp32 = peaks.get("fp32_tflops")
         out["scorer"] = {"kernel": "k_score_seg (exact pair gain, segmented)", "pair_sample_evals_per_s": rate,
-                         "avg_launch_ms": score_ms / max(launches, 1), "launches": int(launches)}
+                         "avg_launch_ms": score_ms / max(launches, 1), "launches": int(launches),
+                         "block_width": z1["tuned_threads"] or 256,
+                         "block_width_tuned": bool(z1["tuned_threads"])}
         if l2:
             out["scorer"]["roofline_l2"] = {"bound": "l2", "achieved": rate * 4.125 / 1e9, "peak": l2, "unit": "GB/s",
                                             "frac": rate * 4.125 / 1e9 / l2,
@@ -385,7 +387,8 @@ def _c4_leg(R, stream, peaks):
         rate = pairs * wl.M / (ms / 1e3)
         ent = {"best_pairs_s": e0.elapsed_time(e1) / 3e3, "scorer_ms_per_search": ms / 3,
                "pairs_scored_per_search": pairs // 3, "pair_sample_evals_per_s": rate,
-               "block_width": s1["tuned_threads"], "knn_iters": s1["knn_iters"]}
+               "block_width": s1["tuned_threads"] or 256, "block_width_tuned": bool(s1["tuned_threads"]),
+               "knn_iters": s1["knn_iters"]}
         gbs = pairs * mp * 8 / (ms / 1e3) / 1e9
         if peaks.get("l2_read_gbs"):
             ent["roofline_l2"] = {"bound": "l2", "achieved": gbs, "peak": peaks["l2_read_gbs"], "unit": "GB/s",
