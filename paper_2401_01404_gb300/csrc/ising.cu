@@ -336,7 +336,10 @@ __device__ __forceinline__ void solve_pair(const RS &R, int Mp, float Hsum, floa
 
 // Both rows in shared memory (row j in a staging buffer), the spins as the
 // lane's transposed bit columns: the Newton passes of a staged candidate touch
-// no global memory
+// no global memory.  The scorer builds it with the lower-numbered node of the
+// pair as row i, so that the solve sees every pair in one orientation and both
+// nodes' blocks give it the same score bit for bit (the passes add the two
+// nodes' terms in a fixed order).
 struct StageRows {
     static constexpr int kNW = 0;
     // (pass 0 of a staged candidate is pass0_consume: only the Newton and gain
@@ -646,7 +649,14 @@ __global__ void __maxnreg__(80) k_score_seg(IsingView v, WTable W, ScoreParams p
             float su, sv;
             int dis;
             pass0_consume<NW>(st, lane, Tx, Tj, ci, tj, cj, su, sv, dis);
-            StageRows R{st, row, ci, cj, v.Mw, lane};
+            // one orientation per pair: the lower-numbered node first
+            const bool sw = cgj[u] < gx;
+            if (sw) {
+                const float tmp = su;
+                su = sv;
+                sv = tmp;
+            }
+            const StageRows R = sw ? StageRows{row, st, cj, ci, v.Mw, lane} : StageRows{st, row, ci, cj, v.Mw, lane};
             float g, w;
             int passes = 0;
             if (p.grad_only)

@@ -132,3 +132,31 @@ def test_device_loop_matches_host_loop(R):
     assert 1 <= iters[0] <= max_iters and 1 <= iters[1] <= max_iters
     assert abs(iters[0] - iters[1]) <= 2
     assert rec[0] > 0.8 and abs(rec[0] - rec[1]) < 0.03, rec
+
+
+@pytest.mark.parametrize("N,M", [(2000, 400), (1500, 1000), (800, 37)])
+def test_pair_scores_do_not_depend_on_the_block(R, N, M):
+    """The segmented scorer solves every pair in one orientation (the
+    lower-numbered node first), so a pair found from both ends of the k-NN graph
+    carries the same d in both lists, bit for bit, also after GCD steps (W != 0:
+    Newton passes); otherwise two FindBest levels could report one pair twice
+    with d values that differ in the last bit."""
+    X = _wl(N, M, 321 + N)
+    Xs = np.ascontiguousarray(X.T)
+    c = R.Recon(Xs, R.RECON_ISING, lam=inputs.default_lambda(N, M))
+    both_total = 0
+    for step in range(3):
+        c.best_pairs(16, 1.0)
+        ids, d = c.knn_graph()
+        seen = {}
+        for x in range(ids.shape[0]):
+            for y, dv in zip(ids[x].tolist(), d[x].tolist()):
+                if y >= 0:
+                    seen[(x, y)] = dv
+        both = [(a, b) for (a, b) in seen if a < b and (b, a) in seen]
+        both_total += len(both)
+        bad = [(a, b, seen[(a, b)], seen[(b, a)]) for a, b in both if seen[(a, b)] != seen[(b, a)]]
+        assert not bad, (step, len(bad), bad[:3])
+        c.gcd_step(16, 1.0)
+    assert both_total > 100
+    c.close()
