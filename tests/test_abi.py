@@ -83,3 +83,39 @@ def test_argument_errors_without_a_gpu(libpath):
     with pytest.raises(recon.ReconError) as e:
         recon.recon_init(np.ones((4, 3), dtype=np.int8), options=recon.recon_default_options(lam=-1.0))
     assert e.value.status == recon.RECON_EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures (options, statistics, device ceilings,
+    training options) have the header's size and field offsets: a field added on
+    one side only would shift every later field silently.  Checked by compiling
+    a small C program against include/recon.h with the host compiler."""
+    import ctypes
+    import shutil
+
+    from paper_2401_01404_gb300 import recon as R
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no host C compiler")
+    structs = {"recon_options": R.recon_options, "recon_stats": R.recon_stats, "recon_peaks": R.recon_peaks,
+               "recon_train_opts": R.recon_train_opts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "recon.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            cfield = fname.rstrip("_")  # (lambda_ in Python is lambda in C)
+            lines.append(f'    printf("{cname}.{fname} %zu\\n", offsetof({cname}, {cfield}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                               check=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
